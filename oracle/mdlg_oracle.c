@@ -466,10 +466,14 @@ int or_md_run(int64_t n, double *x, double *y, double *vx, double *vy, double L,
             if (s < n_equil || (s - n_equil) % every[k] != 0) continue;
             double *sx = snap + 2 * nn * (size_t)k, *sy = sx + nn;
             if (s > n_equil) {
-                for (int32_t d = 0; d < n_dx; ++d)
+                /* the displacement moments belong to the interval, not to a
+                 * lattice: they are accumulated once per window */
+                for (int32_t d = 0; d < n_dx; ++d) {
+                    double dummy[2] = {0.0, 0.0};
                     or_bin_xy(n, sx, sy, x, y, L, lx[d], W,
                               hist + ((int64_t)k * n_dx + d) * nb,
-                              overflow + (int64_t)k * n_dx + d, mom + 2 * k);
+                              overflow + (int64_t)k * n_dx + d, d == 0 ? mom + 2 * k : dummy);
+                }
                 nwin[k] += 1;
             }
             memcpy(sx, x, sizeof(double) * (size_t)n);

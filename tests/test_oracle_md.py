@@ -133,3 +133,21 @@ def test_small_system_runs_sampling(orc):
     assert list(r["nwin"]) == [5, 2]
     tot = r["hist"].sum(axis=2) + r["overflow"]
     assert np.array_equal(tot, np.array([[5 * 1024] * 2, [2 * 1024] * 2]))
+
+
+def test_moments_independent_of_lattice_count(orc):
+    """mu2, mu4 of Sec. 3(b) are moments of the continuous displacement: adding
+    lattices must not change them, and they equal the directly computed
+    moments of x(t+dt_lg) - x(t)."""
+    n = 1024
+    L = inputs.box_length(n, 0.0784)
+    st = inputs.lattice_gas_state(n, L, 20.0, seed=3)
+    a = orc.md_run(st.x, st.y, st.vx, st.vy, L, 5e-4, 400, every=[400], lx=[101], W=4)
+    b = orc.md_run(st.x, st.y, st.vx, st.vy, L, 5e-4, 400, every=[400], lx=[101, 45, 14], W=4)
+    assert np.array_equal(a["mom"], b["mom"])
+    dx = a["x"] - st.x
+    dy = a["y"] - st.y
+    dx -= L * np.round(dx / L)
+    dy -= L * np.round(dy / L)
+    assert abs(a["mom"][0, 0] - np.sum(dx ** 2 + dy ** 2)) < 1e-9 * a["mom"][0, 0]
+    assert abs(a["mom"][0, 1] - np.sum(dx ** 4 + dy ** 4)) < 1e-9 * a["mom"][0, 1]
