@@ -1,0 +1,270 @@
+/*
+ * mdlg.h -- C-ABI of libmdlg.so, the GB300 (sm_103a) hot path of the
+ * molecular-dynamics lattice-gas (MDLG) equilibrium analysis of
+ * Pachalieva & Wagner, arXiv 2101.01160.
+ *
+ * What the library computes
+ *   * 2D Lennard-Jones molecular dynamics (Sec. 4): V = 4 eps [(s/r)^12 -
+ *     (s/r)^6] truncated at rc and shifted to zero there (force not shifted),
+ *     periodic square box, NVE velocity Verlet.
+ *   * The MDLG coarse-graining fused into the time step (Sec. 2): every S MD
+ *     steps each particle's lattice cell at t and t - S dt is compared and
+ *     the integer displacement v_i is counted, i.e. the occupation numbers
+ *     n_i(x,t) of Eq. (n_i) summed over all lattice sites x, accumulated over
+ *     windows into the global histogram behind f_i^eq of Eq. (theory_feq);
+ *     the displacement moments mu2, mu4 of Sec. 3(b) are accumulated beside.
+ *   * The analytic equilibria of Sec. 3: the single-Gaussian f^{eq,G}
+ *     (Eqs. feq_prod, feq_gaussian), the Poisson weighted sum of Gaussians
+ *     f^{eq,WSG} (Eq. f_eq_wsg) and its collision rate lambda from the
+ *     moments (Eq. lambda_eq), and the comparison measures of Eq. (k_Xi) /
+ *     Eq. (kullback_leibler).
+ *
+ * Conventions
+ *   * Every function returns MD_OK (0) or a negative MD_E_* code; no C++
+ *     exception crosses the ABI.  md_last_error() gives a message for the
+ *     calling thread's last failure.
+ *   * "stream" is a cudaStream_t passed as void* (NULL = legacy default
+ *     stream).  Work is enqueued asynchronously on it unless a function says
+ *     it synchronises.
+ *   * Pointers documented "host or device" may be either (the copy uses
+ *     unified addressing); "device" means device memory the caller owns.
+ *     The library never frees caller memory.  A md_system owns only its own
+ *     state and scratch, released by md_destroy.
+ *   * Lattice-velocity tables have (2W+1)^2 entries, entry (vy+W)(2W+1) +
+ *     (vx+W) for the displacement (vx, vy), |vx|,|vy| <= W.
+ *   * Positions are in sigma units on [0, L); the library stores them as a
+ *     cell index plus an offset (FP32 or FP64) and reports L_eff = ncell*h,
+ *     the box edge it actually simulates (equal to the requested L to FP64
+ *     rounding for MD_FP64, to FP32 rounding of h for MD_FP32_CELLOFF).
+ */
+#ifndef MDLG_H
+#define MDLG_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ------------------------------------------------------ */
+#define MD_OK 0
+#define MD_E_ARG -1        /* invalid argument (message says which)          */
+#define MD_E_CUDA -2       /* CUDA runtime error                            */
+#define MD_E_TIMEOUT -3    /* a bounded device-side wait gave up            */
+#define MD_E_SKIN -4       /* a particle moved more than skin/2 between two  */
+                           /* cell-list rebuilds (forces may have missed     */
+                           /* pairs); raise skin                            */
+#define MD_E_NONFINITE -5  /* a non-finite position or velocity was seen     */
+#define MD_E_DOMAIN -6     /* kurtosis outside the range with a real lambda  */
+#define MD_E_NOMEM -7      /* device allocation failed                      */
+#define MD_E_LIMIT -8      /* a size exceeds a documented maximum           */
+
+/* ---- precision of the MD state ----------------------------------------- */
+#define MD_FP64 0          /* FP64 offsets, velocities and forces            */
+#define MD_FP32_CELLOFF 1  /* integer cell + FP32 in-cell offset, FP32 forces */
+                           /* and velocities; lattice mapping, moments and   */
+                           /* reductions stay FP64                           */
+
+#define MD_MAX_LG 8        /* sampling intervals per system                 */
+#define MD_MAX_DX 4        /* lattice spacings per system                   */
+#define MD_MAX_W 10        /* largest displacement window half-width        */
+#define MD_NBLK 32         /* error-bar blocks per histogram                */
+
+/* Parameters of one system (one replica of a batch).  Units: LJ (sigma,
+ * eps, m, tau).  The sampling interval of slot k is Delta t_LG =
+ * lg_every[k]*dt (Sec. 4, "output frequency" times the MD step); lattice d
+ * has lx[d] cells per edge, spacing L_eff/lx[d]. */
+typedef struct md_params {
+    int64_t n;             /* particles, >= 2                               */
+    double box_L;          /* requested periodic box edge                   */
+    double dt;             /* MD time step                                  */
+    double rc;             /* LJ cutoff (2.5 in the configured workloads)    */
+    double eps, sigma, mass;
+    double skin;           /* cell edge is >= rc + skin; a cell list is     */
+                           /* rebuilt once any particle strays 0.4*skin     */
+                           /* outside its cell                               */
+    int32_t precision;     /* MD_FP64 or MD_FP32_CELLOFF                     */
+    int32_t W;             /* displacement window half-width, 1..MD_MAX_W   */
+    int64_t n_equil;       /* MD steps before the first snapshot            */
+    int32_t n_lg;          /* sampling intervals in use, 0..MD_MAX_LG       */
+    int32_t lg_every[MD_MAX_LG];
+    int32_t n_dx;          /* lattices in use, 1..MD_MAX_DX                 */
+    int32_t lx[MD_MAX_DX]; /* lattice cells per box edge                    */
+    int32_t block_windows; /* windows per error-bar block (>= 1)            */
+    int32_t reserved;
+} md_params;
+
+typedef struct md_system md_system;   /* opaque, library-owned */
+
+/* Snapshot of positions in the (cell, offset) encoding: the position of
+ * particle j is x = cx*h + off_x[j], y = cy*h + off_y[j] (FP64 arithmetic,
+ * each product and sum rounded separately), with cell[j] = cy*ncell + cx.
+ * Offsets may lie outside [0, h) (a stale cell list); positions are taken
+ * modulo the box edge ncell*h. */
+typedef struct md_snapshot {
+    const int32_t *cell;   /* device, [n]                                   */
+    const void *off_x;     /* device, [n] float or double                   */
+    const void *off_y;     /* device, [n] float or double                   */
+    int32_t off_is_f64;    /* 0: float offsets, 1: double offsets           */
+    int32_t ncell;         /* cells per box edge                            */
+    double h;              /* cell edge; box edge L = ncell*h               */
+} md_snapshot;
+
+/* Information about a system, filled by md_info. */
+typedef struct md_info_t {
+    int64_t n_total;       /* particles over all replicas                   */
+    int64_t step;          /* completed MD steps                            */
+    int64_t n_rebuilds;    /* cell-list rebuilds so far                     */
+    int32_t n_rep;
+    int32_t precision;
+    int32_t grid_blocks;   /* persistent-kernel CTAs                        */
+    int32_t block_threads;
+} md_info_t;
+
+typedef struct md_rep_info_t {
+    int64_t n;
+    double L_eff;          /* ncell*h                                       */
+    double h;              /* MD cell edge                                  */
+    int32_t ncell;
+    int32_t reserved;
+    double dx_eff[MD_MAX_DX]; /* L_eff / lx[d]                              */
+} md_rep_info_t;
+
+/* Measured equilibrium of one (replica, interval, lattice), see feq_measured. */
+typedef struct md_feq_stats {
+    double mu2;            /* <dx_alpha^2> per axis over all samples         */
+    double mu4;            /* <dx_alpha^4>                                  */
+    double a2;             /* mu2 / dx_eff^2 (Eq. a2_n_ua)                  */
+    double dx_eff;
+    int64_t n_windows;     /* sampling windows accumulated                  */
+    int64_t n_samples;     /* particle-windows = sum(hist) + n_overflow     */
+    int64_t n_overflow;    /* displacements outside the window             */
+    int64_t n_blocks_used; /* error-bar blocks holding data                 */
+} md_feq_stats;
+
+/* ---- system lifecycle ---------------------------------------------------- */
+
+/* Creates a system of one replica from an initial state (Sec. 4: homogeneous
+ * positions, kinetic energy at the target temperature, zero momentum; the
+ * caller generates it).  x, y, vx, vy: host or device, FP64, [p->n],
+ * particle-id order; positions are wrapped into the box.  Velocities are
+ * taken as the velocities at step 0.  Synchronises the stream.  On success
+ * *out owns device memory until md_destroy. */
+int md_init(const md_params *p, const double *x, const double *y, const double *vx,
+            const double *vy, void *stream, md_system **out);
+
+/* Creates a batch of n_rep independent replicas advanced together by one
+ * persistent kernel.  p[r] are the per-replica parameters; precision, W,
+ * n_equil, n_lg, lg_every, n_dx and block_windows must agree over all
+ * replicas (lx, L, n, dt, ... may differ).  The state arrays hold the
+ * replicas back to back in replica order (sum of p[r].n entries). */
+int md_init_batch(const md_params *p, int32_t n_rep, const double *x, const double *y,
+                  const double *vx, const double *vy, void *stream, md_system **out);
+
+void md_destroy(md_system *s);
+
+/* Advances every replica by nsteps velocity-Verlet steps (Sec. 4) in one
+ * persistent cooperative kernel, sampling the MDLG histograms (Sec. 2) on
+ * every step t = n_equil + m*lg_every[k] and rebuilding cell lists as
+ * needed.  Asynchronous on the system's stream; device-side failures
+ * (MD_E_TIMEOUT, MD_E_SKIN, MD_E_NONFINITE) are reported by md_sync. */
+int md_step(md_system *s, int64_t nsteps);
+
+/* Waits for the system's stream and returns the device status word (and
+ * clears it). */
+int md_sync(md_system *s);
+
+int md_info(md_system *s, md_info_t *out);
+int md_rep_info(md_system *s, int32_t rep, md_rep_info_t *out);
+
+/* Positions (wrapped into [0, L_eff)) and velocities at the current step, in
+ * particle-id order over all replicas; host or device outputs, FP64.
+ * Completes the half kick if needed (the trajectory continues bit for bit
+ * as if not called).  Synchronises. */
+int md_get_state(md_system *s, double *x, double *y, double *vx, double *vy);
+
+/* Replaces positions and velocities (same layout as md_init); keeps the
+ * histograms and the step counter.  Synchronises. */
+int md_set_state(md_system *s, const double *x, const double *y, const double *vx,
+                 const double *vy);
+
+/* Raw current positions in the snapshot encoding, particle-id order:
+ * cell (linear cy*ncell+cx), offsets as float (MD_FP32_CELLOFF) or double
+ * (MD_FP64).  Device outputs.  Synchronises. */
+int md_get_raw(md_system *s, int32_t *cell, void *off_x, void *off_y);
+
+/* The snapshot held for sampling interval lg (positions at the last
+ * sampling time), same encoding as md_get_raw. Device outputs. Synchronises. */
+int md_get_snapshot(md_system *s, int32_t lg, int32_t *cell, void *off_x, void *off_y);
+
+/* Forces at the current positions, FP64, particle-id order, host or device
+ * outputs; fabs_sum (may be NULL) receives sum_j |F_ij| per particle.
+ * Synchronises. */
+int md_forces(md_system *s, double *fx, double *fy, double *fabs_sum);
+
+/* Energy of replica rep at the current step: out4 = {kinetic, shifted
+ * potential, P_x, P_y} (host, FP64).  Synchronises. */
+int md_energy(md_system *s, int32_t rep, double *out4);
+
+/* Raw integer histogram totals of (rep, lg, dxi): hist (host, int64,
+ * (2W+1)^2), *overflow, *n_windows (host).  Synchronises. */
+int md_hist_raw(md_system *s, int32_t rep, int32_t lg, int32_t dxi, int64_t *hist,
+                int64_t *overflow, int64_t *n_windows);
+
+/* Measured equilibrium distribution (Eq. theory_feq, normalised per
+ * particle): P_out[i] = H_i / (N * n_windows), the probability that a
+ * particle's lattice displacement over one interval is v_i; sum(P) = 1 -
+ * overflow fraction.  If symmetrize != 0 each value is replaced by its
+ * symmetric-set average (Sec. 5).  stderr_out (may be NULL) receives the
+ * batch-means standard error over error-bar blocks.  Normalisation runs on
+ * the device in FP64; outputs are host memory.  Synchronises. */
+int feq_measured(md_system *s, int32_t rep, int32_t lg, int32_t dxi, int32_t symmetrize,
+                 double *P_out, double *stderr_out, md_feq_stats *stats);
+
+/* ---- MDLG binning of two snapshots (Sec. 2, Eq. n_i) -------------------- */
+
+/* Lattice displacement histogram of n particles between snapshots t0 and t1
+ * (same ncell and h): lattice index l = floor(x / dxl) mod lx per axis,
+ * dxl = ncell*h/lx, displacement = nearest periodic image of l1 - l0; inside
+ * the window it counts in hist_out, else in *overflow_out.  mom_out[0] =
+ * sum of delta^2, mom_out[1] = sum of delta^4 over particles and both axes
+ * for the continuous nearest-image displacement delta.  Outputs (device)
+ * are overwritten.  Bit-exact integer results: the FP64 arithmetic is
+ * rounded operation by operation.  n < 2^31. */
+int mdlg_bin(const md_snapshot *t0, const md_snapshot *t1, int64_t n, int32_t lx, int32_t W,
+             int32_t *hist_out, int64_t *overflow_out, double *mom_out, void *stream);
+
+/* ---- analytic equilibria (Sec. 3) ---------------------------------------- */
+
+/* Single-Gaussian equilibrium, Eqs. (feq_prod), (feq_gaussian): P_out[i] =
+ * f_i^{eq,G}/rho = g(vx - ux) g(vy - uy), a2 = <dx^2>/dx^2, (ux, uy) the mean
+ * velocity in lattice units.  P_out: device, (2W+1)^2 doubles. */
+int feq_gaussian(double a2, double ux, double uy, int32_t W, double *P_out, void *stream);
+
+/* Mean collision number lambda from the measured moments, Eq. (lambda_eq):
+ * root 1 takes the '+' sign of the square root, root 2 (the paper's choice)
+ * the '-' sign.  *lambda_out: device double.  If the kurtosis mu4/mu2^2 is
+ * <= 3 (no excess: the mixture degenerates to one Gaussian) 0 is written; if
+ * it exceeds 3.75 (no real root) 1 is written (the double root at 3.75);
+ * both return MD_E_DOMAIN. */
+int wsg_lambda(double mu2, double mu4, int32_t root, double *lambda_out, void *stream);
+
+/* Poisson weighted sum of Gaussians equilibrium, Eq. (f_eq_wsg): P_out[i] =
+ * sum_c Pois(c; lambda) f^c(vx-ux) f^c(vy-uy), N_c = sqrt(2 a2 (c+1) /
+ * (lambda+1)); terms c = 0..ceil(lambda + 12 sqrt(lambda) + 20) (omitted
+ * Poisson tail < 1e-16).  P_out: device, (2W+1)^2 doubles. */
+int feq_wsg(double a2, double lambda, double ux, double uy, int32_t W, double *P_out,
+            void *stream);
+
+/* Comparison of two distributions over n classes (Sec. 3, Eqs. k_Xi,
+ * kullback_leibler): out3 (device) = {max_i |R_i - Q_i|, D_KL(R||Q) with
+ * 0 log 0 = 0, sum_i R_i}.  R, Q: device. */
+int feq_compare(const double *R, const double *Q, int32_t n, double *out3, void *stream);
+
+/* Message of the calling thread's last failure ("" if none). */
+const char *md_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* MDLG_H */

@@ -1,0 +1,734 @@
+// Host side of the MD system: md_init / md_init_batch / md_step / readouts.
+//
+// One system holds one or more replicas.  md_step enqueues a single
+// cooperative launch of the persistent kernel (md_kernels.cuh) that runs all
+// requested steps, sampling and cell-list rebuilds on the device; control
+// returns to the host only at md_sync or at a readout.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <vector>
+
+#include "common.cuh"
+#include "md_kernels.cuh"
+
+namespace mdlg {
+
+template <typename T>
+__global__ void k_init(SysDev S, const double *x, const double *y, const double *vx,
+                       const double *vy) {
+    using V = typename V2<T>::type;
+    const int slot = blockIdx.x * blockDim.x + threadIdx.x;
+    if (slot < S.nrep) {
+        const RepDev &R = S.reps[slot];
+        S.cellcnt[R.cbase + R.nc * R.nc] = R.cap - R.n;
+    }
+    if (slot >= S.nslots) return;
+    const RepDev &R = S.reps[S.gran_rep[slot / GRAN]];
+    const int local = slot - R.pbase;
+    V *pos = static_cast<V *>(S.pos[0][0]);
+    V *vel = static_cast<V *>(S.vel[0]);
+    if (local >= R.n) {
+        pos[slot] = V{T(0), T(0)};
+        vel[slot] = V{T(0), T(0)};
+        S.cell[0][slot] = 0u;
+        S.pid[0][slot] = -1;
+        return;
+    }
+    const int id = R.ibase + local;
+    double X = x[id], Y = y[id];
+    X -= R.L * floor(X / R.L);
+    Y -= R.L * floor(Y / R.L);
+    if (X >= R.L) X -= R.L;
+    if (Y >= R.L) Y -= R.L;
+    int cx = (int)floor(X / R.h), cy = (int)floor(Y / R.h);
+    cx = min(max(cx, 0), R.nc - 1);
+    cy = min(max(cy, 0), R.nc - 1);
+    pos[slot] = V{(T)(X - (double)cx * R.h), (T)(Y - (double)cy * R.h)};
+    vel[slot] = V{(T)vx[id], (T)vy[id]};
+    S.cell[0][slot] = (uint32_t)cx | ((uint32_t)cy << 16);
+    S.pid[0][slot] = id;
+}
+
+// Energy partials of one replica summed in a fixed order.
+__global__ void k_sum_energy(const double *epart, int g0, int g1, double *out4) {
+    __shared__ double sh[4][256];
+    double a[4] = {0, 0, 0, 0};
+    for (int g = g0 + threadIdx.x; g < g1; g += 256)
+        for (int k = 0; k < 4; ++k) a[k] += epart[(long long)g * 4 + k];
+    for (int k = 0; k < 4; ++k) sh[k][threadIdx.x] = a[k];
+    __syncthreads();
+    for (int o = 128; o > 0; o >>= 1) {
+        if ((int)threadIdx.x < o)
+            for (int k = 0; k < 4; ++k) sh[k][threadIdx.x] += sh[k][threadIdx.x + o];
+        __syncthreads();
+    }
+    if (threadIdx.x < 4) out4[threadIdx.x] = sh[threadIdx.x][0];
+}
+
+struct FeqArgs {
+    const int32_t *hist;          // [MD_NBLK][nb] of one (rep, lg, dx)
+    const unsigned long long *ovf;
+    const double *mom;            // [ngran32][n_lg][2]
+    int g0, g1, n_lg, lg, nb, W, sym;
+    double n;                     // particles of the replica
+    long long nwin;
+    long long wblk[MD_NBLK];      // windows per block
+    double dx_eff;
+    double *out;                  // [nb] P, [nb] stderr, [8] stats
+};
+
+// Normalised measured equilibrium (Eq. theory_feq per particle), batch-means
+// error bars over blocks of windows, optional symmetric-set averaging
+// (Sec. 5), moments mu2, mu4 and a^2 (Eq. a2_n_ua).  One CTA.
+constexpr int FEQ_THREADS = 128;
+
+__global__ void __launch_bounds__(FEQ_THREADS) k_feq_measured(FeqArgs A) {
+    __shared__ double s2[FEQ_THREADS], s4[FEQ_THREADS];
+    double m2 = 0.0, m4 = 0.0;
+    for (int g = A.g0 + threadIdx.x; g < A.g1; g += blockDim.x) {
+        m2 += A.mom[((long long)g * A.n_lg + A.lg) * 2];
+        m4 += A.mom[((long long)g * A.n_lg + A.lg) * 2 + 1];
+    }
+    s2[threadIdx.x] = m2;
+    s4[threadIdx.x] = m4;
+    __syncthreads();
+    for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+        if ((int)threadIdx.x < o) {
+            s2[threadIdx.x] += s2[threadIdx.x + o];
+            s4[threadIdx.x] += s4[threadIdx.x + o];
+        }
+        __syncthreads();
+    }
+    const double samples = A.n * (double)A.nwin;
+    const int side = 2 * A.W + 1;
+    for (int i = threadIdx.x; i < A.nb; i += blockDim.x) {
+        int mem[8];
+        int nm = 0;
+        if (A.sym) {
+            const int a = abs(i % side - A.W), b = abs(i / side - A.W);
+            const int lo = min(a, b), hi = max(a, b);
+            for (int j = 0; j < A.nb && nm < 8; ++j) {
+                const int c = abs(j % side - A.W), d = abs(j / side - A.W);
+                if (min(c, d) == lo && max(c, d) == hi) mem[nm++] = j;
+            }
+        } else {
+            mem[nm++] = i;
+        }
+        long long tot = 0;
+        double pb[MD_NBLK];
+        for (int b = 0; b < MD_NBLK; ++b) {
+            long long hb = 0;
+            for (int m = 0; m < nm; ++m) hb += A.hist[b * A.nb + mem[m]];
+            tot += hb;
+            pb[b] = A.wblk[b] > 0 ? (double)hb / ((double)nm * A.n * (double)A.wblk[b]) : 0.0;
+        }
+        const double P = samples > 0 ? (double)tot / ((double)nm * samples) : 0.0;
+        double num = 0.0, wsum = 0.0;
+        int used = 0;
+        for (int b = 0; b < MD_NBLK; ++b) {
+            if (A.wblk[b] <= 0) continue;
+            const double w = (double)A.wblk[b];
+            num += w * w * (pb[b] - P) * (pb[b] - P);
+            wsum += w;
+            ++used;
+        }
+        A.out[i] = P;
+        A.out[A.nb + i] = used > 1 ? sqrt(num / (wsum * wsum) * (double)used / (double)(used - 1)) : 0.0;
+    }
+    if (threadIdx.x == 0) {
+        double *st = A.out + 2 * A.nb;
+        const double mu2 = samples > 0 ? s2[0] / (2.0 * samples) : 0.0;
+        const double mu4 = samples > 0 ? s4[0] / (2.0 * samples) : 0.0;
+        st[0] = mu2;
+        st[1] = mu4;
+        st[2] = mu2 / (A.dx_eff * A.dx_eff);
+        st[3] = (double)(*A.ovf);
+    }
+}
+
+__global__ void k_hist_total(const int32_t *hist, int nb, long long *out) {
+    for (int i = threadIdx.x; i < nb; i += blockDim.x) {
+        long long t = 0;
+        for (int b = 0; b < MD_NBLK; ++b) t += hist[b * nb + i];
+        out[i] = t;
+    }
+}
+
+__global__ void k_copy_snapshot(const uint32_t *sc, const void *so, int f64, long long ntot,
+                                const int32_t *nc_of_id, int32_t *cell, void *ox, void *oy) {
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= ntot) return;
+    const uint32_t pk = sc[i];
+    cell[i] = (int32_t)(pk >> 16) * nc_of_id[i] + (int32_t)(pk & 0xffffu);
+    if (f64) {
+        const double2 v = static_cast<const double2 *>(so)[i];
+        static_cast<double *>(ox)[i] = v.x;
+        static_cast<double *>(oy)[i] = v.y;
+    } else {
+        const float2 v = static_cast<const float2 *>(so)[i];
+        static_cast<float *>(ox)[i] = v.x;
+        static_cast<float *>(oy)[i] = v.y;
+    }
+}
+
+__global__ void k_nc_of_id(SysDev S, int32_t *nc_of_id) {
+    const int slot = blockIdx.x * blockDim.x + threadIdx.x;
+    if (slot >= S.nslots) return;
+    const RepDev &R = S.reps[S.gran_rep[slot / GRAN]];
+    const int local = slot - R.pbase;
+    if (local < R.n) nc_of_id[R.ibase + local] = R.nc;
+}
+
+}  // namespace mdlg
+
+using namespace mdlg;
+
+struct md_system {
+    int prec = 0, nrep = 0, W = 0, nb = 0, n_lg = 0, n_dx = 0, block_windows = 1;
+    int lg_every[MD_MAX_LG] = {0};
+    long long n_equil = 0;
+    std::vector<RepDev> reps;
+    long long ntot = 0;
+    int nslots = 0, total_cells = 0;
+    cudaStream_t st = nullptr;
+    int dev = 0, nsm = 1;
+    int block = 256, grid = 1;
+    size_t smem = 0;
+    long long step = 0;
+    int phase_half = 0;
+    std::vector<void *> allocs;
+    SysDev sd{};
+    RepDev *d_reps = nullptr;
+    int32_t *d_gran = nullptr;
+    Control *d_ctl = nullptr;
+    double *d_epart = nullptr;
+    double *d_small = nullptr;   // readout scratch (2*nb + 8 doubles, 4 energy)
+    long long *d_hist64 = nullptr;
+    int32_t *d_nc_of_id = nullptr;
+};
+
+namespace {
+
+int dalloc(md_system *s, void **p, size_t bytes) {
+    if (bytes == 0) bytes = 16;
+    cudaError_t e = cudaMalloc(p, bytes);
+    if (e != cudaSuccess) {
+        *p = nullptr;
+        return fail(MD_E_NOMEM, "cudaMalloc(%zu): %s", bytes, cudaGetErrorString(e));
+    }
+    s->allocs.push_back(*p);
+    return MD_OK;
+}
+
+const void *persistent_fn(int prec, int block) {
+    if (prec == MD_FP64)
+        return block == 128 ? (const void *)k_md_persistent<double, 128>
+                            : (const void *)k_md_persistent<double, 256>;
+    return block == 128 ? (const void *)k_md_persistent<float, 128>
+                        : (const void *)k_md_persistent<float, 256>;
+}
+
+int configure_launch(md_system *s, int block) {
+    const void *fn = persistent_fn(s->prec, block);
+    s->smem = (size_t)s->n_lg * s->n_dx * s->nb * sizeof(int);
+    MD_CUDA_TRY(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)std::max<size_t>(s->smem, 0)));
+    int occ = 0;
+    MD_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, block, s->smem));
+    if (occ < 1) return fail(MD_E_CUDA, "persistent kernel does not fit on an SM");
+    const long long maxco = (long long)occ * s->nsm;
+    const long long nchunks = s->nslots / block;
+    const long long q = (nchunks + maxco - 1) / maxco;
+    s->grid = (int)std::min<long long>(4096, std::max<long long>(1, (nchunks + q - 1) / q));
+    s->block = block;
+    return MD_OK;
+}
+
+int launch_persistent(md_system *s, long long nsteps, int force_rebuild) {
+    const void *fn = persistent_fn(s->prec, s->block);
+    long long step0 = s->step;
+    int phase = s->phase_half;
+    void *args[] = {&s->sd, &step0, &nsteps, &phase, &force_rebuild};
+    MD_CUDA_TRY(cudaLaunchCooperativeKernel(fn, dim3(s->grid), dim3(s->block), args, s->smem, s->st));
+    return MD_OK;
+}
+
+int status_to_code(int ds) {
+    if (ds & DS_TIMEOUT) return fail(MD_E_TIMEOUT, "device barrier wait timed out");
+    if (ds & DS_NONFINITE) return fail(MD_E_NONFINITE, "non-finite position encountered");
+    if (ds & DS_SKIN) return fail(MD_E_SKIN, "a particle moved more than one cell in one step");
+    return MD_OK;
+}
+
+int sync_status(md_system *s) {
+    MD_CUDA_TRY(cudaStreamSynchronize(s->st));
+    int ds = 0;
+    MD_CUDA_TRY(cudaMemcpy(&ds, &s->d_ctl->status, sizeof(int), cudaMemcpyDeviceToHost));
+    if (ds) {
+        MD_CUDA_TRY(cudaMemset(&s->d_ctl->status, 0, sizeof(int)));
+        return status_to_code(ds);
+    }
+    return MD_OK;
+}
+
+int check_params(const md_params *p, int r, const md_params *p0) {
+    if (p->n < 2 || p->n > (1ll << 30)) return fail(MD_E_ARG, "replica %d: n out of [2, 2^30]", r);
+    if (!(p->box_L > 0) || !(p->dt > 0) || !(p->rc > 0) || !(p->sigma > 0) || !(p->mass > 0) ||
+        !(p->eps >= 0) || !(p->skin > 0))
+        return fail(MD_E_ARG, "replica %d: box_L, dt, rc, sigma, mass, skin must be > 0, eps >= 0", r);
+    if (p->precision != MD_FP64 && p->precision != MD_FP32_CELLOFF)
+        return fail(MD_E_ARG, "replica %d: unknown precision", r);
+    if (p->W < 1 || p->W > MD_MAX_W) return fail(MD_E_ARG, "W out of [1,%d]", MD_MAX_W);
+    if (p->n_lg < 0 || p->n_lg > MD_MAX_LG) return fail(MD_E_ARG, "n_lg out of [0,%d]", MD_MAX_LG);
+    if (p->n_dx < 1 || p->n_dx > MD_MAX_DX) return fail(MD_E_ARG, "n_dx out of [1,%d]", MD_MAX_DX);
+    for (int k = 0; k < p->n_lg; ++k)
+        if (p->lg_every[k] < 1) return fail(MD_E_ARG, "lg_every[%d] must be >= 1", k);
+    for (int d = 0; d < p->n_dx; ++d)
+        if (p->lx[d] < 1) return fail(MD_E_ARG, "replica %d: lx[%d] must be >= 1", r, d);
+    if (p->n_equil < 0) return fail(MD_E_ARG, "n_equil must be >= 0");
+    if (p->block_windows < 1) return fail(MD_E_ARG, "block_windows must be >= 1");
+    const long long nc = (long long)std::floor(p->box_L / (p->rc + p->skin));
+    if (nc < 3) return fail(MD_E_ARG, "replica %d: box must hold >= 3 cells of rc+skin", r);
+    if (nc > 32767) return fail(MD_E_LIMIT, "replica %d: more than 32767 cells per edge", r);
+    if (p0) {
+        if (p->precision != p0->precision || p->W != p0->W || p->n_equil != p0->n_equil ||
+            p->n_lg != p0->n_lg || p->n_dx != p0->n_dx || p->block_windows != p0->block_windows)
+            return fail(MD_E_ARG, "replica %d: batch-wide parameters differ from replica 0", r);
+        for (int k = 0; k < p->n_lg; ++k)
+            if (p->lg_every[k] != p0->lg_every[k])
+                return fail(MD_E_ARG, "replica %d: lg_every differs from replica 0", r);
+    }
+    return MD_OK;
+}
+
+int observe(md_system *s, ObsArgs a);
+
+int upload_state(md_system *s, const double *x, const double *y, const double *vx,
+                 const double *vy) {
+    if (!x || !y || !vx || !vy) return fail(MD_E_ARG, "state arrays must not be NULL");
+    const size_t bytes = sizeof(double) * (size_t)s->ntot;
+    double *tmp = nullptr;
+    MD_CUDA_TRY(cudaMallocAsync((void **)&tmp, 4 * bytes, s->st));
+    int rc = MD_OK;
+    const double *src[4] = {x, y, vx, vy};
+    for (int k = 0; k < 4 && rc == MD_OK; ++k) {
+        cudaError_t e = cudaMemcpyAsync(tmp + k * s->ntot, src[k], bytes, cudaMemcpyDefault, s->st);
+        if (e != cudaSuccess) rc = fail(MD_E_CUDA, "state upload: %s", cudaGetErrorString(e));
+    }
+    if (rc == MD_OK) {
+        // fresh cell list: positions go to set 0, buffer 0
+        cudaMemsetAsync(&s->d_ctl->set, 0, 2 * sizeof(int), s->st);
+        const int nthr = 256;
+        const int nblk = (s->nslots + nthr - 1) / nthr;
+        if (s->prec == MD_FP64)
+            k_init<double><<<nblk, nthr, 0, s->st>>>(s->sd, tmp, tmp + s->ntot, tmp + 2 * s->ntot,
+                                                     tmp + 3 * s->ntot);
+        else
+            k_init<float><<<nblk, nthr, 0, s->st>>>(s->sd, tmp, tmp + s->ntot, tmp + 2 * s->ntot,
+                                                    tmp + 3 * s->ntot);
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) rc = fail(MD_E_CUDA, "init kernel: %s", cudaGetErrorString(e));
+    }
+    if (rc == MD_OK) rc = launch_persistent(s, 0, 1);
+    cudaFreeAsync(tmp, s->st);
+    if (rc) return rc;
+    s->phase_half = 0;
+    // a state placed on a sampling boundary starts the next window there
+    unsigned mask = 0;
+    for (int k = 0; k < s->n_lg; ++k)
+        if (s->step >= s->n_equil && (s->step - s->n_equil) % s->lg_every[k] == 0) mask |= 1u << k;
+    if (mask) {
+        ObsArgs a{};
+        a.snap_mask = mask;
+        rc = observe(s, a);
+        if (rc) return rc;
+    }
+    return sync_status(s);
+}
+
+// Runs the observation kernel; completes the half kick when needed.
+int observe(md_system *s, ObsArgs a) {
+    a.complete = s->phase_half;
+    const int nthr = 256;
+    const int nblk = s->nslots / nthr;
+    if (s->prec == MD_FP64)
+        k_observe<double><<<nblk, nthr, 0, s->st>>>(s->sd, a);
+    else
+        k_observe<float><<<nblk, nthr, 0, s->st>>>(s->sd, a);
+    MD_CUDA_TRY(cudaGetLastError());
+    s->phase_half = 0;
+    return MD_OK;
+}
+
+long long windows_done(const md_system *s, int k) {
+    const long long t = s->step - s->n_equil;
+    if (t < 0) return 0;
+    return t / s->lg_every[k];
+}
+
+}  // namespace
+
+extern "C" {
+
+int md_init_batch(const md_params *p, int32_t n_rep, const double *x, const double *y,
+                  const double *vx, const double *vy, void *stream, md_system **out) {
+    if (!p || !out || n_rep < 1) return fail(MD_E_ARG, "md_init_batch: bad arguments");
+    *out = nullptr;
+    for (int r = 0; r < n_rep; ++r) {
+        int rc = check_params(&p[r], r, r ? &p[0] : nullptr);
+        if (rc) return rc;
+    }
+    md_system *s = new md_system();
+    s->st = (cudaStream_t)stream;
+    s->prec = p[0].precision;
+    s->nrep = n_rep;
+    s->W = p[0].W;
+    s->nb = (2 * s->W + 1) * (2 * s->W + 1);
+    s->n_lg = p[0].n_lg;
+    s->n_dx = p[0].n_dx;
+    s->block_windows = p[0].block_windows;
+    s->n_equil = p[0].n_equil;
+    for (int k = 0; k < s->n_lg; ++k) s->lg_every[k] = p[0].lg_every[k];
+    long long pbase = 0, cbase = 0, ibase = 0;
+    for (int r = 0; r < n_rep; ++r) {
+        const md_params &q = p[r];
+        RepDev R{};
+        R.nc = (int)std::floor(q.box_L / (q.rc + q.skin));
+        double h = q.box_L / R.nc;
+        if (s->prec == MD_FP32_CELLOFF) h = (double)(float)h;
+        R.h = h;
+        R.L = (double)R.nc * h;
+        R.n = (int)q.n;
+        R.cap = (int)((q.n + SLOT_PAD - 1) / SLOT_PAD * SLOT_PAD);
+        R.pbase = (int)pbase;
+        R.cbase = (int)cbase;
+        R.ibase = (int)ibase;
+        R.dt = q.dt;
+        R.hk = q.dt / (2.0 * q.mass);
+        R.rc2 = q.rc * q.rc;
+        R.eps = q.eps;
+        R.sig2 = q.sigma * q.sigma;
+        const double sc2 = q.sigma * q.sigma / (q.rc * q.rc), sc6 = sc2 * sc2 * sc2;
+        R.vshift = 4.0 * q.eps * (sc6 * sc6 - sc6);
+        R.mass = q.mass;
+        R.trig_lo = -0.45 * q.skin;
+        R.trig_hi = h + 0.45 * q.skin;
+        for (int d = 0; d < s->n_dx; ++d) {
+            R.lx[d] = q.lx[d];
+            R.dxl[d] = R.L / (double)q.lx[d];
+        }
+        R.hf = (float)h;
+        R.dtf = (float)R.dt;
+        R.hkf = (float)R.hk;
+        R.rc2f = (float)R.rc2;
+        R.epsf = (float)R.eps;
+        R.sig2f = (float)R.sig2;
+        R.trig_lof = (float)R.trig_lo;
+        R.trig_hif = (float)R.trig_hi;
+        s->reps.push_back(R);
+        pbase += R.cap;
+        cbase += (long long)R.nc * R.nc + 1;
+        ibase += q.n;
+    }
+    if (pbase >= (1ll << 31) - SLOT_PAD || cbase >= (1ll << 31) - 1) {
+        delete s;
+        return fail(MD_E_LIMIT, "md_init_batch: more than 2^31 slots or cells");
+    }
+    s->nslots = (int)pbase;
+    s->total_cells = (int)cbase;
+    s->ntot = ibase;
+    int rc = MD_OK;
+    cudaError_t e = cudaGetDevice(&s->dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&s->nsm, cudaDevAttrMultiProcessorCount, s->dev);
+    if (e != cudaSuccess) {
+        delete s;
+        return fail(MD_E_CUDA, "md_init_batch: %s", cudaGetErrorString(e));
+    }
+    const size_t vsz = s->prec == MD_FP64 ? sizeof(double2) : sizeof(float2);
+    const size_t ns = (size_t)s->nslots, nlg = (size_t)std::max(1, s->n_lg);
+    const size_t ngr = ns / 32;
+    SysDev &S = s->sd;
+#define ALLOC(ptr, bytes) \
+    if (rc == MD_OK) rc = dalloc(s, (void **)&(ptr), (bytes))
+    ALLOC(s->d_reps, sizeof(RepDev) * n_rep);
+    ALLOC(s->d_gran, sizeof(int32_t) * (ns / GRAN));
+    ALLOC(s->d_ctl, sizeof(Control));
+    for (int k = 0; k < 2; ++k) {
+        ALLOC(S.cell[k], sizeof(uint32_t) * ns);
+        ALLOC(S.pid[k], sizeof(int32_t) * ns);
+        ALLOC(S.vel[k], vsz * ns);
+        ALLOC(S.pos[k][0], vsz * ns);
+        ALLOC(S.pos[k][1], vsz * ns);
+    }
+    ALLOC(S.cellcnt, sizeof(int32_t) * s->total_cells);
+    ALLOC(S.cell_start, sizeof(int32_t) * (s->total_cells + 1));
+    ALLOC(S.newcell, sizeof(int32_t) * ns);
+    ALLOC(S.rank, sizeof(int32_t) * ns);
+    ALLOC(S.perm, sizeof(int32_t) * ns);
+    ALLOC(S.blocksum, sizeof(int32_t) * 4096);
+    ALLOC(S.snap_cell, sizeof(uint32_t) * nlg * s->ntot);
+    ALLOC(S.snap_off, vsz * nlg * s->ntot);
+    const size_t nhist = (size_t)n_rep * nlg * s->n_dx * MD_NBLK * s->nb;
+    ALLOC(S.hist, sizeof(int32_t) * nhist);
+    ALLOC(S.ovf, sizeof(unsigned long long) * n_rep * nlg * s->n_dx);
+    ALLOC(S.mom, sizeof(double) * ngr * nlg * 2);
+    ALLOC(s->d_epart, sizeof(double) * ngr * 4);
+    ALLOC(s->d_small, sizeof(double) * (2 * s->nb + 16));
+    ALLOC(s->d_hist64, sizeof(long long) * s->nb);
+    ALLOC(s->d_nc_of_id, sizeof(int32_t) * s->ntot);
+#undef ALLOC
+    if (rc) {
+        md_destroy(s);
+        return rc;
+    }
+    std::vector<int32_t> gran(ns / GRAN);
+    for (int r = 0; r < n_rep; ++r)
+        for (int g = s->reps[r].pbase / GRAN; g < (s->reps[r].pbase + s->reps[r].cap) / GRAN; ++g)
+            gran[g] = r;
+    S.reps = s->d_reps;
+    S.gran_rep = s->d_gran;
+    S.ctl = s->d_ctl;
+    S.nslots = s->nslots;
+    S.nrep = n_rep;
+    S.total_cells = s->total_cells;
+    S.n_lg = s->n_lg;
+    S.n_dx = s->n_dx;
+    S.W = s->W;
+    S.nb = s->nb;
+    S.block_windows = s->block_windows;
+    S.n_equil = s->n_equil;
+    for (int k = 0; k < MD_MAX_LG; ++k) S.lg_every[k] = s->lg_every[k];
+    S.ntot = s->ntot;
+    S.timeout_ns = 4000000000ull;
+    auto tryc = [&](cudaError_t er) {
+        if (er != cudaSuccess && rc == MD_OK) rc = fail(MD_E_CUDA, "md_init_batch: %s", cudaGetErrorString(er));
+    };
+    tryc(cudaMemcpyAsync(s->d_reps, s->reps.data(), sizeof(RepDev) * n_rep, cudaMemcpyHostToDevice, s->st));
+    tryc(cudaMemcpyAsync(s->d_gran, gran.data(), sizeof(int32_t) * gran.size(), cudaMemcpyHostToDevice, s->st));
+    tryc(cudaMemsetAsync(s->d_ctl, 0, sizeof(Control), s->st));
+    tryc(cudaMemsetAsync(S.cellcnt, 0, sizeof(int32_t) * s->total_cells, s->st));
+    tryc(cudaMemsetAsync(S.hist, 0, sizeof(int32_t) * nhist, s->st));
+    tryc(cudaMemsetAsync(S.ovf, 0, sizeof(unsigned long long) * n_rep * nlg * s->n_dx, s->st));
+    tryc(cudaMemsetAsync(S.mom, 0, sizeof(double) * ngr * nlg * 2, s->st));
+    tryc(cudaMemsetAsync(S.snap_cell, 0, sizeof(uint32_t) * nlg * s->ntot, s->st));
+    tryc(cudaMemsetAsync(S.snap_off, 0, vsz * nlg * s->ntot, s->st));
+    if (rc == MD_OK) {
+        k_nc_of_id<<<(s->nslots + 255) / 256, 256, 0, s->st>>>(S, s->d_nc_of_id);
+        tryc(cudaGetLastError());
+    }
+    if (rc == MD_OK) rc = configure_launch(s, 256);
+    if (rc == MD_OK) rc = upload_state(s, x, y, vx, vy);
+    if (rc) {
+        md_destroy(s);
+        return rc;
+    }
+    *out = s;
+    return MD_OK;
+}
+
+int md_init(const md_params *p, const double *x, const double *y, const double *vx,
+            const double *vy, void *stream, md_system **out) {
+    return md_init_batch(p, 1, x, y, vx, vy, stream, out);
+}
+
+void md_destroy(md_system *s) {
+    if (!s) return;
+    if (s->st) cudaStreamSynchronize(s->st);
+    for (void *p : s->allocs) cudaFree(p);
+    delete s;
+}
+
+int md_step(md_system *s, int64_t nsteps) {
+    if (!s || nsteps < 0) return fail(MD_E_ARG, "md_step: bad arguments");
+    if (nsteps == 0) return MD_OK;
+    int rc = launch_persistent(s, nsteps, 0);
+    if (rc) return rc;
+    s->step += nsteps;
+    s->phase_half = 1;
+    return MD_OK;
+}
+
+int md_sync(md_system *s) {
+    if (!s) return fail(MD_E_ARG, "md_sync: NULL system");
+    return sync_status(s);
+}
+
+int md_info(md_system *s, md_info_t *o) {
+    if (!s || !o) return fail(MD_E_ARG, "md_info: NULL argument");
+    MD_CUDA_TRY(cudaStreamSynchronize(s->st));
+    Control c;
+    MD_CUDA_TRY(cudaMemcpy(&c, s->d_ctl, sizeof(Control), cudaMemcpyDeviceToHost));
+    o->n_total = s->ntot;
+    o->step = s->step;
+    o->n_rebuilds = c.n_rebuilds;
+    o->n_rep = s->nrep;
+    o->precision = s->prec;
+    o->grid_blocks = s->grid;
+    o->block_threads = s->block;
+    return MD_OK;
+}
+
+int md_rep_info(md_system *s, int32_t rep, md_rep_info_t *o) {
+    if (!s || !o || rep < 0 || rep >= s->nrep) return fail(MD_E_ARG, "md_rep_info: bad arguments");
+    const RepDev &R = s->reps[rep];
+    o->n = R.n;
+    o->L_eff = R.L;
+    o->h = R.h;
+    o->ncell = R.nc;
+    o->reserved = 0;
+    for (int d = 0; d < MD_MAX_DX; ++d) o->dx_eff[d] = d < s->n_dx ? R.dxl[d] : 0.0;
+    return MD_OK;
+}
+
+int md_get_state(md_system *s, double *x, double *y, double *vx, double *vy) {
+    if (!s || !x || !y || !vx || !vy) return fail(MD_E_ARG, "md_get_state: NULL argument");
+    const size_t bytes = sizeof(double) * s->ntot;
+    double *tmp = nullptr;
+    MD_CUDA_TRY(cudaMallocAsync((void **)&tmp, 4 * bytes, s->st));
+    ObsArgs a{};
+    a.x = tmp;
+    a.y = tmp + s->ntot;
+    a.vx = tmp + 2 * s->ntot;
+    a.vy = tmp + 3 * s->ntot;
+    int rc = observe(s, a);
+    double *dst[4] = {x, y, vx, vy};
+    for (int k = 0; k < 4 && rc == MD_OK; ++k) {
+        cudaError_t e = cudaMemcpyAsync(dst[k], tmp + k * s->ntot, bytes, cudaMemcpyDefault, s->st);
+        if (e != cudaSuccess) rc = fail(MD_E_CUDA, "md_get_state: %s", cudaGetErrorString(e));
+    }
+    cudaFreeAsync(tmp, s->st);
+    if (rc) return rc;
+    return sync_status(s);
+}
+
+int md_set_state(md_system *s, const double *x, const double *y, const double *vx,
+                 const double *vy) {
+    if (!s) return fail(MD_E_ARG, "md_set_state: NULL system");
+    return upload_state(s, x, y, vx, vy);
+}
+
+int md_get_raw(md_system *s, int32_t *cell, void *off_x, void *off_y) {
+    if (!s || !cell || !off_x || !off_y) return fail(MD_E_ARG, "md_get_raw: NULL argument");
+    ObsArgs a{};
+    a.raw_cell = cell;
+    a.raw_x = off_x;
+    a.raw_y = off_y;
+    int rc = observe(s, a);
+    if (rc) return rc;
+    return sync_status(s);
+}
+
+int md_get_snapshot(md_system *s, int32_t lg, int32_t *cell, void *off_x, void *off_y) {
+    if (!s || !cell || !off_x || !off_y || lg < 0 || lg >= s->n_lg)
+        return fail(MD_E_ARG, "md_get_snapshot: bad arguments");
+    const size_t vsz = s->prec == MD_FP64 ? sizeof(double2) : sizeof(float2);
+    k_copy_snapshot<<<(unsigned)((s->ntot + 255) / 256), 256, 0, s->st>>>(
+        s->sd.snap_cell + (size_t)lg * s->ntot, (const char *)s->sd.snap_off + vsz * lg * s->ntot,
+        s->prec == MD_FP64, s->ntot, s->d_nc_of_id, cell, off_x, off_y);
+    MD_CUDA_TRY(cudaGetLastError());
+    return sync_status(s);
+}
+
+int md_forces(md_system *s, double *fx, double *fy, double *fabs_sum) {
+    if (!s || !fx || !fy) return fail(MD_E_ARG, "md_forces: NULL argument");
+    const size_t bytes = sizeof(double) * s->ntot;
+    double *tmp = nullptr;
+    MD_CUDA_TRY(cudaMallocAsync((void **)&tmp, 3 * bytes, s->st));
+    ObsArgs a{};
+    a.fx = tmp;
+    a.fy = tmp + s->ntot;
+    a.fabs_sum = tmp + 2 * s->ntot;
+    int rc = observe(s, a);
+    double *dst[3] = {fx, fy, fabs_sum};
+    for (int k = 0; k < 3 && rc == MD_OK; ++k) {
+        if (!dst[k]) continue;
+        cudaError_t e = cudaMemcpyAsync(dst[k], tmp + k * s->ntot, bytes, cudaMemcpyDefault, s->st);
+        if (e != cudaSuccess) rc = fail(MD_E_CUDA, "md_forces: %s", cudaGetErrorString(e));
+    }
+    cudaFreeAsync(tmp, s->st);
+    if (rc) return rc;
+    return sync_status(s);
+}
+
+int md_energy(md_system *s, int32_t rep, double *out4) {
+    if (!s || !out4 || rep < 0 || rep >= s->nrep) return fail(MD_E_ARG, "md_energy: bad arguments");
+    ObsArgs a{};
+    a.epart = s->d_epart;
+    int rc = observe(s, a);
+    if (rc) return rc;
+    const RepDev &R = s->reps[rep];
+    k_sum_energy<<<1, 256, 0, s->st>>>(s->d_epart, R.pbase / 32, (R.pbase + R.cap) / 32, s->d_small);
+    MD_CUDA_TRY(cudaGetLastError());
+    MD_CUDA_TRY(cudaMemcpyAsync(out4, s->d_small, 4 * sizeof(double), cudaMemcpyDeviceToHost, s->st));
+    return sync_status(s);
+}
+
+int md_hist_raw(md_system *s, int32_t rep, int32_t lg, int32_t dxi, int64_t *hist,
+                int64_t *overflow, int64_t *n_windows) {
+    if (!s || !hist || rep < 0 || rep >= s->nrep || lg < 0 || lg >= s->n_lg || dxi < 0 ||
+        dxi >= s->n_dx)
+        return fail(MD_E_ARG, "md_hist_raw: bad arguments");
+    const size_t base = ((size_t)(rep * s->n_lg + lg) * s->n_dx + dxi);
+    k_hist_total<<<1, 256, 0, s->st>>>(s->sd.hist + base * MD_NBLK * s->nb, s->nb, s->d_hist64);
+    MD_CUDA_TRY(cudaGetLastError());
+    MD_CUDA_TRY(cudaMemcpyAsync(hist, s->d_hist64, sizeof(int64_t) * s->nb, cudaMemcpyDeviceToHost, s->st));
+    unsigned long long ov = 0;
+    MD_CUDA_TRY(cudaMemcpyAsync(&ov, s->sd.ovf + base, sizeof(ov), cudaMemcpyDeviceToHost, s->st));
+    int rc = sync_status(s);
+    if (rc) return rc;
+    if (overflow) *overflow = (int64_t)ov;
+    if (n_windows) *n_windows = windows_done(s, lg);
+    return MD_OK;
+}
+
+int feq_measured(md_system *s, int32_t rep, int32_t lg, int32_t dxi, int32_t symmetrize,
+                 double *P_out, double *stderr_out, md_feq_stats *stats) {
+    if (!s || !P_out || rep < 0 || rep >= s->nrep || lg < 0 || lg >= s->n_lg || dxi < 0 ||
+        dxi >= s->n_dx)
+        return fail(MD_E_ARG, "feq_measured: bad arguments");
+    const RepDev &R = s->reps[rep];
+    const size_t base = ((size_t)(rep * s->n_lg + lg) * s->n_dx + dxi);
+    FeqArgs A{};
+    A.hist = s->sd.hist + base * MD_NBLK * s->nb;
+    A.ovf = s->sd.ovf + base;
+    A.mom = s->sd.mom;
+    A.g0 = R.pbase / 32;
+    A.g1 = (R.pbase + R.cap) / 32;
+    A.n_lg = s->n_lg;
+    A.lg = lg;
+    A.nb = s->nb;
+    A.W = s->W;
+    A.sym = symmetrize != 0;
+    A.n = (double)R.n;
+    A.nwin = windows_done(s, lg);
+    int used = 0;
+    for (long long w = 0; w < A.nwin; ++w) {
+        const int b = (int)((w / s->block_windows) % MD_NBLK);
+        if (A.wblk[b]++ == 0) ++used;
+    }
+    A.dx_eff = R.dxl[dxi];
+    A.out = s->d_small;
+    k_feq_measured<<<1, FEQ_THREADS, 0, s->st>>>(A);
+    MD_CUDA_TRY(cudaGetLastError());
+    std::vector<double> h(2 * s->nb + 8);
+    MD_CUDA_TRY(cudaMemcpyAsync(h.data(), s->d_small, sizeof(double) * h.size(), cudaMemcpyDeviceToHost, s->st));
+    int rc = sync_status(s);
+    if (rc) return rc;
+    std::memcpy(P_out, h.data(), sizeof(double) * s->nb);
+    if (stderr_out) std::memcpy(stderr_out, h.data() + s->nb, sizeof(double) * s->nb);
+    if (stats) {
+        const double *st = h.data() + 2 * s->nb;
+        stats->mu2 = st[0];
+        stats->mu4 = st[1];
+        stats->a2 = st[2];
+        stats->dx_eff = A.dx_eff;
+        stats->n_windows = A.nwin;
+        stats->n_overflow = (int64_t)st[3];
+        stats->n_samples = (int64_t)R.n * A.nwin;
+        stats->n_blocks_used = used;
+    }
+    return MD_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,301 @@
+"""Thin Python binding of libmdlg.so (C-ABI in include/mdlg.h).
+
+Argument marshalling only: every computation runs in the library's CUDA
+kernels.  Device buffers are torch CUDA tensors (their data_ptr() is passed);
+streams are torch streams (the current stream by default).  If the library is
+missing this module raises instead of falling back to anything else.
+"""
+
+from __future__ import annotations
+
+import ctypes as C
+import os
+from dataclasses import dataclass, field
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SO = os.path.join(_HERE, "libmdlg.so")
+_lib = None
+
+MD_OK = 0
+MD_E_ARG, MD_E_CUDA, MD_E_TIMEOUT, MD_E_SKIN, MD_E_NONFINITE, MD_E_DOMAIN, MD_E_NOMEM, MD_E_LIMIT = \
+    -1, -2, -3, -4, -5, -6, -7, -8
+MD_FP64, MD_FP32_CELLOFF = 0, 1
+MD_MAX_LG, MD_MAX_DX, MD_MAX_W, MD_NBLK = 8, 4, 10, 32
+
+
+class MDError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"libmdlg error {code}: {msg}")
+        self.code = code
+
+
+class md_params(C.Structure):
+    _fields_ = [
+        ("n", C.c_int64), ("box_L", C.c_double), ("dt", C.c_double), ("rc", C.c_double),
+        ("eps", C.c_double), ("sigma", C.c_double), ("mass", C.c_double), ("skin", C.c_double),
+        ("precision", C.c_int32), ("W", C.c_int32), ("n_equil", C.c_int64),
+        ("n_lg", C.c_int32), ("lg_every", C.c_int32 * MD_MAX_LG),
+        ("n_dx", C.c_int32), ("lx", C.c_int32 * MD_MAX_DX),
+        ("block_windows", C.c_int32), ("reserved", C.c_int32),
+    ]
+
+
+class md_snapshot(C.Structure):
+    _fields_ = [("cell", C.c_void_p), ("off_x", C.c_void_p), ("off_y", C.c_void_p),
+                ("off_is_f64", C.c_int32), ("ncell", C.c_int32), ("h", C.c_double)]
+
+
+class md_info_t(C.Structure):
+    _fields_ = [("n_total", C.c_int64), ("step", C.c_int64), ("n_rebuilds", C.c_int64),
+                ("n_rep", C.c_int32), ("precision", C.c_int32), ("grid_blocks", C.c_int32),
+                ("block_threads", C.c_int32)]
+
+
+class md_rep_info_t(C.Structure):
+    _fields_ = [("n", C.c_int64), ("L_eff", C.c_double), ("h", C.c_double),
+                ("ncell", C.c_int32), ("reserved", C.c_int32),
+                ("dx_eff", C.c_double * MD_MAX_DX)]
+
+
+class md_feq_stats(C.Structure):
+    _fields_ = [("mu2", C.c_double), ("mu4", C.c_double), ("a2", C.c_double),
+                ("dx_eff", C.c_double), ("n_windows", C.c_int64), ("n_samples", C.c_int64),
+                ("n_overflow", C.c_int64), ("n_blocks_used", C.c_int64)]
+
+
+P = C.c_void_p
+_SIGS = {
+    "md_init": ([C.POINTER(md_params), P, P, P, P, P, C.POINTER(P)], C.c_int),
+    "md_init_batch": ([C.POINTER(md_params), C.c_int32, P, P, P, P, P, C.POINTER(P)], C.c_int),
+    "md_destroy": ([P], None),
+    "md_step": ([P, C.c_int64], C.c_int),
+    "md_sync": ([P], C.c_int),
+    "md_info": ([P, C.POINTER(md_info_t)], C.c_int),
+    "md_rep_info": ([P, C.c_int32, C.POINTER(md_rep_info_t)], C.c_int),
+    "md_get_state": ([P, P, P, P, P], C.c_int),
+    "md_set_state": ([P, P, P, P, P], C.c_int),
+    "md_get_raw": ([P, P, P, P], C.c_int),
+    "md_get_snapshot": ([P, C.c_int32, P, P, P], C.c_int),
+    "md_forces": ([P, P, P, P], C.c_int),
+    "md_energy": ([P, C.c_int32, P], C.c_int),
+    "md_hist_raw": ([P, C.c_int32, C.c_int32, C.c_int32, P, P, P], C.c_int),
+    "feq_measured": ([P, C.c_int32, C.c_int32, C.c_int32, C.c_int32, P, P,
+                      C.POINTER(md_feq_stats)], C.c_int),
+    "mdlg_bin": ([C.POINTER(md_snapshot), C.POINTER(md_snapshot), C.c_int64, C.c_int32, C.c_int32,
+                  P, P, P, P], C.c_int),
+    "feq_gaussian": ([C.c_double, C.c_double, C.c_double, C.c_int32, P, P], C.c_int),
+    "wsg_lambda": ([C.c_double, C.c_double, C.c_int32, P, P], C.c_int),
+    "feq_wsg": ([C.c_double, C.c_double, C.c_double, C.c_double, C.c_int32, P, P], C.c_int),
+    "feq_compare": ([P, P, C.c_int32, P, P], C.c_int),
+    "md_last_error": ([], C.c_char_p),
+}
+
+
+def library_path() -> str:
+    return _SO
+
+
+def load():
+    """Loads libmdlg.so; raises if it has not been built."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(_SO):
+            raise ImportError(f"libmdlg.so not built ({_SO}); run __graft_entry__.build()")
+        lib = C.CDLL(_SO)
+        for name, (args, res) in _SIGS.items():
+            fn = getattr(lib, name)
+            fn.argtypes = args
+            fn.restype = res
+        _lib = lib
+    return _lib
+
+
+def _check(rc):
+    if rc != MD_OK:
+        msg = load().md_last_error().decode(errors="replace")
+        raise MDError(rc, msg)
+    return rc
+
+
+def _stream(stream=None):
+    import torch
+
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return C.c_void_p(s.cuda_stream)
+
+
+def _ptr(a):
+    """Device pointer of a torch tensor, or host pointer of a numpy array."""
+    if a is None:
+        return None
+    if isinstance(a, np.ndarray):
+        assert a.flags.c_contiguous
+        return C.c_void_p(a.ctypes.data)
+    assert a.is_contiguous()
+    return C.c_void_p(a.data_ptr())
+
+
+def make_params(n, L, dt=5e-4, rc=2.5, eps=1.0, sigma=1.0, mass=1.0, skin=0.5,
+                precision=MD_FP32_CELLOFF, W=4, n_equil=0, lg_every=(400,), lx=(101,),
+                block_windows=1) -> md_params:
+    p = md_params()
+    p.n, p.box_L, p.dt, p.rc, p.eps, p.sigma, p.mass, p.skin = n, L, dt, rc, eps, sigma, mass, skin
+    p.precision, p.W, p.n_equil = precision, W, n_equil
+    p.n_lg = len(lg_every)
+    for k, v in enumerate(lg_every):
+        p.lg_every[k] = int(v)
+    p.n_dx = len(lx)
+    for k, v in enumerate(lx):
+        p.lx[k] = int(v)
+    p.block_windows = block_windows
+    return p
+
+
+class System:
+    """A system of one or more replicas (md_init / md_init_batch)."""
+
+    def __init__(self, params, x, y, vx, vy, stream=None):
+        lib = load()
+        if isinstance(params, md_params):
+            params = [params]
+        self.params = list(params)
+        arr = (md_params * len(self.params))(*self.params)
+        self._keep = [np.ascontiguousarray(a, dtype=np.float64) if isinstance(a, np.ndarray) else a
+                      for a in (x, y, vx, vy)]
+        h = P()
+        self._stream = _stream(stream)
+        _check(lib.md_init_batch(arr, len(self.params), *[_ptr(a) for a in self._keep],
+                                 self._stream, C.byref(h)))
+        self.h = h
+        self._keep = None
+        self.n_total = int(sum(p.n for p in self.params))
+        self.prec = self.params[0].precision
+        self.nb = (2 * self.params[0].W + 1) ** 2
+
+    def close(self):
+        if getattr(self, "h", None):
+            load().md_destroy(self.h)
+            self.h = None
+
+    __del__ = close
+
+    def step(self, nsteps):
+        _check(load().md_step(self.h, int(nsteps)))
+
+    def sync(self):
+        _check(load().md_sync(self.h))
+
+    def info(self):
+        o = md_info_t()
+        _check(load().md_info(self.h, C.byref(o)))
+        return o
+
+    def rep_info(self, rep=0):
+        o = md_rep_info_t()
+        _check(load().md_rep_info(self.h, rep, C.byref(o)))
+        return o
+
+    def get_state(self):
+        out = [np.zeros(self.n_total) for _ in range(4)]
+        _check(load().md_get_state(self.h, *[_ptr(a) for a in out]))
+        return out
+
+    def set_state(self, x, y, vx, vy):
+        arrs = [np.ascontiguousarray(a, dtype=np.float64) for a in (x, y, vx, vy)]
+        _check(load().md_set_state(self.h, *[_ptr(a) for a in arrs]))
+
+    def _raw_buffers(self):
+        import torch
+
+        ft = torch.float64 if self.prec == MD_FP64 else torch.float32
+        cell = torch.empty(self.n_total, dtype=torch.int32, device="cuda")
+        ox = torch.empty(self.n_total, dtype=ft, device="cuda")
+        oy = torch.empty(self.n_total, dtype=ft, device="cuda")
+        return cell, ox, oy
+
+    def get_raw(self):
+        cell, ox, oy = self._raw_buffers()
+        _check(load().md_get_raw(self.h, _ptr(cell), _ptr(ox), _ptr(oy)))
+        return cell, ox, oy
+
+    def get_snapshot(self, lg):
+        cell, ox, oy = self._raw_buffers()
+        _check(load().md_get_snapshot(self.h, lg, _ptr(cell), _ptr(ox), _ptr(oy)))
+        return cell, ox, oy
+
+    def forces(self):
+        fx, fy, fa = (np.zeros(self.n_total) for _ in range(3))
+        _check(load().md_forces(self.h, _ptr(fx), _ptr(fy), _ptr(fa)))
+        return fx, fy, fa
+
+    def energy(self, rep=0):
+        out = np.zeros(4)
+        _check(load().md_energy(self.h, rep, _ptr(out)))
+        return out
+
+    def hist_raw(self, rep=0, lg=0, dxi=0):
+        hist = np.zeros(self.nb, np.int64)
+        ov = C.c_int64()
+        nw = C.c_int64()
+        _check(load().md_hist_raw(self.h, rep, lg, dxi, _ptr(hist), C.byref(ov), C.byref(nw)))
+        return hist, ov.value, nw.value
+
+    def feq_measured(self, rep=0, lg=0, dxi=0, symmetrize=False):
+        Pm = np.zeros(self.nb)
+        se = np.zeros(self.nb)
+        st = md_feq_stats()
+        _check(load().feq_measured(self.h, rep, lg, dxi, int(symmetrize), _ptr(Pm), _ptr(se),
+                                   C.byref(st)))
+        return Pm, se, st
+
+
+def mdlg_bin(cell0, ox0, oy0, cell1, ox1, oy1, ncell, h, lx, W, stream=None):
+    """Histogram of lattice displacements between two device snapshots."""
+    import torch
+
+    f64 = int(ox0.dtype == torch.float64)
+    s0 = md_snapshot(_ptr(cell0).value, _ptr(ox0).value, _ptr(oy0).value, f64, ncell, h)
+    s1 = md_snapshot(_ptr(cell1).value, _ptr(ox1).value, _ptr(oy1).value, f64, ncell, h)
+    nb = (2 * W + 1) ** 2
+    hist = torch.empty(nb, dtype=torch.int32, device="cuda")
+    ovf = torch.empty(1, dtype=torch.int64, device="cuda")
+    mom = torch.empty(2, dtype=torch.float64, device="cuda")
+    _check(load().mdlg_bin(C.byref(s0), C.byref(s1), cell0.numel(), lx, W, _ptr(hist),
+                           _ptr(ovf), _ptr(mom), _stream(stream)))
+    return hist, ovf, mom
+
+
+def feq_gaussian(a2, ux=0.0, uy=0.0, W=4, stream=None):
+    import torch
+
+    out = torch.empty((2 * W + 1) ** 2, dtype=torch.float64, device="cuda")
+    _check(load().feq_gaussian(a2, ux, uy, W, _ptr(out), _stream(stream)))
+    return out
+
+
+def wsg_lambda(mu2, mu4, root=2, stream=None, allow_domain=False):
+    import torch
+
+    out = torch.empty(1, dtype=torch.float64, device="cuda")
+    rc = load().wsg_lambda(mu2, mu4, root, _ptr(out), _stream(stream))
+    if not (allow_domain and rc == MD_E_DOMAIN):
+        _check(rc)
+    return out, rc
+
+
+def feq_wsg(a2, lam, ux=0.0, uy=0.0, W=4, stream=None):
+    import torch
+
+    out = torch.empty((2 * W + 1) ** 2, dtype=torch.float64, device="cuda")
+    _check(load().feq_wsg(a2, lam, ux, uy, W, _ptr(out), _stream(stream)))
+    return out
+
+
+def feq_compare(R, Q, stream=None):
+    import torch
+
+    out = torch.empty(3, dtype=torch.float64, device="cuda")
+    _check(load().feq_compare(_ptr(R), _ptr(Q), R.numel(), _ptr(out), _stream(stream)))
+    return out

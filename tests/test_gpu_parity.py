@@ -1,0 +1,350 @@
+"""GPU parity of the CUDA path against the FP64 CPU oracle, through the C-ABI.
+
+Tolerances (stated once here, used below):
+  * integer coarse-graining (histograms, overflow): bit-exact;
+  * analytic f_eq (Gaussian, WSG), lambda, KL: 1e-12 absolute (the required
+    bound is 1e-6; the kernels evaluate the same closed forms in FP64);
+  * forces: |F_gpu - F_oracle| <= tol * sum_j |F_ij| per particle and axis,
+    tol = 1e-12 (FP64) and 1e-5 (FP32 cell+offset); an isolated particle's
+    force is exactly 0;
+  * moment sums: 1e-12 relative (FP64 sums in a different order).
+"""
+
+import math
+
+import numpy as np
+import pytest
+
+from paper_2101_01160_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+def _dev(a, dt=None):
+    t = torch.from_numpy(np.ascontiguousarray(a))
+    if dt is not None:
+        t = t.to(dt)
+    return t.cuda()
+
+
+@pytest.mark.parametrize("f64", [False, True])
+@pytest.mark.parametrize("n", [0, 1, 31, 1000, 262_147])
+def test_mdlg_bin_bitexact(mdlg, orc, f64, n):
+    ncell, h = 33, 101.283 / 33
+    if f64 is False:
+        h = float(np.float32(h))
+    s = inputs.random_celloff_snapshots(n, ncell, h, seed=n + 7, max_step=6.0, f64=f64,
+                                        ties=min(n, 300), lattice_dx=ncell * h / 101)
+    for lx, W in ((101, 4), (50, 2), (203, 10), (7, 1)):
+        hist, ovf, mom = mdlg.mdlg_bin(*[_dev(s[k]) for k in ("cell0", "ox0", "oy0", "cell1",
+                                                               "ox1", "oy1")],
+                                       ncell, h, lx, W)
+        torch.cuda.synchronize()
+        rh, ro, rm = orc.bin_celloff(s, ncell, h, ncell * h, lx, W)
+        assert np.array_equal(hist.cpu().numpy().astype(np.int64), rh)
+        assert int(ovf.item()) == ro
+        assert int(hist.sum().item()) + int(ovf.item()) == n
+        m = mom.cpu().numpy()
+        assert np.allclose(m, rm, rtol=1e-12, atol=1e-300)
+
+
+def test_mdlg_bin_rejects_bad_args(mdlg):
+    c = torch.zeros(4, dtype=torch.int32, device="cuda")
+    o = torch.zeros(4, dtype=torch.float32, device="cuda")
+    with pytest.raises(mdlg.MDError):
+        mdlg.mdlg_bin(c, o, o, c, o, o, 10, 1.0, 10, 11)   # W > MD_MAX_W
+    with pytest.raises(mdlg.MDError):
+        mdlg.mdlg_bin(c, o, o, c, o, o, 10, 1.0, 0, 4)     # lx < 1
+
+
+@pytest.mark.parametrize("W", [1, 4, 10])
+def test_feq_analytic_matches_oracle(mdlg, orc, W):
+    for a2 in (1 / 6, 0.1611, 0.05, 0.8, 4.0):
+        for ux, uy in ((0.0, 0.0), (0.3, -0.2)):
+            g = mdlg.feq_gaussian(a2, ux, uy, W).cpu().numpy()
+            assert np.max(np.abs(g - orc.feq_gaussian(a2, ux, uy, W))) < 1e-12
+            for lam in (0.0, 0.38, 2.618, 17.0, 58.0):
+                w = mdlg.feq_wsg(a2, lam, ux, uy, W).cpu().numpy()
+                assert np.max(np.abs(w - orc.feq_wsg(a2, lam, ux, uy, W))) < 1e-12
+
+
+def test_wsg_lambda_and_compare(mdlg, orc):
+    rng = np.random.default_rng(3)
+    for _ in range(20):
+        mu2 = float(rng.uniform(0.05, 3.0))
+        k = float(rng.uniform(3.01, 3.74))
+        rc, l1, l2 = orc.wsg_lambda(mu2, k * mu2 * mu2)
+        g1, _ = mdlg.wsg_lambda(mu2, k * mu2 * mu2, root=1)
+        g2, _ = mdlg.wsg_lambda(mu2, k * mu2 * mu2, root=2)
+        assert abs(g1.item() - l1) < 1e-12 * max(1, l1)
+        assert abs(g2.item() - l2) < 1e-12 * max(1, l2)
+    out, rc = mdlg.wsg_lambda(1.0, 2.9, allow_domain=True)
+    assert rc == mdlg.MD_E_DOMAIN and out.item() == 0.0
+    out, rc = mdlg.wsg_lambda(1.0, 3.9, allow_domain=True)
+    assert rc == mdlg.MD_E_DOMAIN and out.item() == 1.0
+    R = orc.feq_gaussian(0.1611)
+    Q = orc.feq_wsg(0.1611, 2.618)
+    c = mdlg.feq_compare(_dev(R), _dev(Q)).cpu().numpy()
+    assert abs(c[0] - np.max(np.abs(R - Q))) < 1e-15
+    assert abs(c[1] - orc.kl(R, Q)) < 1e-14
+    assert abs(c[2] - R.sum()) < 1e-14
+
+
+def _state(n, phi, T, seed):
+    L = inputs.box_length(n, phi)
+    return inputs.lattice_gas_state(n, L, T, seed=seed), L
+
+
+def _check_forces(gx, gy, ox, oy, fa, tol):
+    scale = fa + 1e-300
+    errx = np.abs(gx - ox)
+    erry = np.abs(gy - oy)
+    iso = fa == 0.0
+    assert np.all(gx[iso] == 0.0) and np.all(gy[iso] == 0.0)
+    assert np.all(errx[~iso] <= tol * scale[~iso] + 1e-300), np.max(errx[~iso] / scale[~iso])
+    assert np.all(erry[~iso] <= tol * scale[~iso] + 1e-300), np.max(erry[~iso] / scale[~iso])
+
+
+@pytest.mark.parametrize("prec,tol", [(0, 1e-12), (1, 1e-5)])
+@pytest.mark.parametrize("n,phi,T", [(1024, 0.0784, 20.0), (5000, 0.35, 1.0), (3000, 0.05, 5.0)])
+def test_forces_match_oracle(mdlg, orc, prec, tol, n, phi, T):
+    st, L = _state(n, phi, T, seed=n)
+    # lattice sites jittered by +-0.3 spacing, so that many pairs interact
+    a = L / math.ceil(math.sqrt(n))
+    rng = np.random.default_rng(n)
+    x = st.x + rng.uniform(-0.3 * a, 0.3 * a, n)
+    y = st.y + rng.uniform(-0.3 * a, 0.3 * a, n)
+    p = mdlg.make_params(n, L, precision=prec, lg_every=(50,), lx=(int(round(L)),))
+    s = mdlg.System(p, x, y, st.vx, st.vy)
+    Le = s.rep_info(0).L_eff
+    gx_, gy_, gvx, gvy = s.get_state()
+    fx, fy, fa = s.forces()
+    ox, oy, _, ofa = orc.forces_cells(gx_, gy_, Le)
+    assert np.allclose(fa, ofa, rtol=1e-4 if prec else 1e-12, atol=1e-9)
+    _check_forces(fx, fy, ox, oy, ofa, tol)
+    assert (ofa > 0).sum() > n // 4
+    s.close()
+
+
+def test_fp64_short_trajectory_matches_oracle(mdlg, orc):
+    st, L = _state(1024, 0.0784, 20.0, seed=2)
+    p = mdlg.make_params(1024, L, precision=mdlg.MD_FP64, lg_every=(100,), lx=(101,))
+    s = mdlg.System(p, st.x, st.y, st.vx, st.vy)
+    Le = s.rep_info(0).L_eff
+    x0, y0, vx0, vy0 = s.get_state()
+    for k in range(3):
+        s.step(100)
+        s.sync()
+    xg, yg, vxg, vyg = s.get_state()
+    r = orc.md_run(x0, y0, vx0, vy0, Le, 5e-4, 300, every=[100], lx=[101], W=4)
+    d = xg - r["x"]
+    d -= Le * np.round(d / Le)
+    assert np.max(np.abs(d)) < 1e-9
+    assert np.max(np.abs(vxg - r["vx"])) < 1e-7
+    hist, ovf, nwin = s.hist_raw()
+    assert nwin == 3
+    assert np.array_equal(hist, r["hist"][0, 0]) and ovf == r["overflow"][0, 0]
+    s.close()
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_fused_binning_bitexact_on_snapshots(mdlg, orc, prec):
+    """The histogram increment of one window equals the oracle's binning of the
+    two snapshots the fused kernel used (bit-exact), on two lattices."""
+    n = 20000
+    st, L = _state(n, 0.0784, 20.0, seed=5)
+    every = 150
+    p = mdlg.make_params(n, L, precision=prec, lg_every=(every, 2 * every),
+                         lx=(int(round(L)), int(round(L / 2))), W=4)
+    s = mdlg.System(p, st.x, st.y, st.vx, st.vy)
+    info = s.rep_info(0)
+    nc, h = info.ncell, info.h
+    s.step(2 * every)
+    snaps = {k: [t.cpu().numpy() for t in s.get_snapshot(k)] for k in (0, 1)}
+    before = {(k, d): s.hist_raw(0, k, d) for k in (0, 1) for d in (0, 1)}
+    s.step(2 * every)
+    after_a = [t.cpu().numpy() for t in s.get_snapshot(0)]
+    for d, lx in enumerate(p.lx[:2]):
+        h1, o1, _ = s.hist_raw(0, 1, d)
+        h0, o0, _ = before[(1, d)]
+        b = snaps[1]
+        a = [t.cpu().numpy() for t in s.get_snapshot(1)]
+        sn = dict(cell0=b[0], ox0=b[1], oy0=b[2], cell1=a[0], ox1=a[1], oy1=a[2])
+        rh, ro, _ = orc.bin_celloff(sn, nc, h, info.L_eff, lx, 4)
+        assert np.array_equal(h1 - h0, rh)
+        assert o1 - o0 == ro
+    assert after_a[0].shape == (n,)
+    s.close()
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_energy_and_momentum_conservation(mdlg, orc, prec):
+    st, L = _state(1024, 0.0784, 20.0, seed=3)
+    p = mdlg.make_params(1024, L, precision=prec, lg_every=(400,), lx=(101,))
+    s = mdlg.System(p, st.x, st.y, st.vx, st.vy)
+    e0 = s.energy()
+    E = [e0[0] + e0[1]]
+    for _ in range(10):
+        s.step(200)
+        e = s.energy()
+        E.append(e[0] + e[1])
+        assert abs(e[2]) < (1e-9 if prec == 0 else 2e-2) and abs(e[3]) < (1e-9 if prec == 0 else 2e-2)
+    E = np.array(E)
+    drift = np.max(np.abs(E - E[0])) / abs(E[0])
+    assert drift < (5e-5 if prec == 0 else 1e-3), drift
+    s.close()
+
+
+def test_get_state_does_not_perturb_trajectory(mdlg):
+    st, L = _state(4096, 0.0784, 20.0, seed=4)
+    p = mdlg.make_params(4096, L, precision=mdlg.MD_FP32_CELLOFF, lg_every=(100,), lx=(int(L),))
+    a = mdlg.System(p, st.x, st.y, st.vx, st.vy)
+    b = mdlg.System(p, st.x, st.y, st.vx, st.vy)
+    a.step(600)
+    b.step(300)
+    b.get_state()
+    b.energy()
+    b.step(300)
+    for u, v in zip(a.get_state(), b.get_state()):
+        assert np.array_equal(u, v)
+    assert np.array_equal(a.hist_raw()[0], b.hist_raw()[0])
+    a.close()
+    b.close()
+
+
+def test_ideal_gas_matches_gaussian(mdlg, orc):
+    """eps = 0: ballistic flight, the measured equilibrium must be the Gaussian
+    one with a^2 = T dt_lg^2 / dx^2 (Sec. 1) within multinomial error."""
+    from scipy import stats
+
+    n, L, T = 200_000, 600.0, 20.0
+    st = inputs.ideal_gas_state(n, L, T, seed=8)
+    every, dt = 200, 5e-4
+    p = mdlg.make_params(n, L, dt=dt, eps=0.0, precision=mdlg.MD_FP32_CELLOFF, lg_every=(every,),
+                         lx=(600,), W=4)
+    s = mdlg.System(p, st.x, st.y, st.vx, st.vy)
+    s.step(every)
+    hist, ovf, nwin = s.hist_raw()
+    assert nwin == 1 and hist.sum() + ovf == n
+    dx_eff = s.rep_info(0).dx_eff[0]
+    a2 = T * (every * dt) ** 2 / dx_eff ** 2
+    P = orc.feq_gaussian(a2, 0.0, 0.0, 4)
+    exp = n * P
+    keep = exp > 20
+    chi2 = float(np.sum((hist[keep] - exp[keep]) ** 2 / exp[keep]))
+    assert stats.chi2.sf(chi2, int(keep.sum()) - 1) > 1e-3
+    s.close()
+
+
+def test_determinism(mdlg):
+    st, L = _state(30000, 0.2, 5.0, seed=6)
+    p = mdlg.make_params(30000, L, precision=mdlg.MD_FP32_CELLOFF, lg_every=(100,), lx=(int(L),))
+    runs = []
+    for _ in range(2):
+        s = mdlg.System(p, st.x, st.y, st.vx, st.vy)
+        s.step(1000)
+        runs.append((s.get_state(), s.hist_raw(), s.feq_measured()[2].mu2, s.info().n_rebuilds))
+        s.close()
+    (a, ha, ma, ra), (b, hb, mb, rb) = runs
+    for u, v in zip(a, b):
+        assert np.array_equal(u, v)
+    assert np.array_equal(ha[0], hb[0]) and ma == mb and ra == rb and ra > 0
+
+
+def _orbit_mean(P, W=4):
+    side = 2 * W + 1
+    keys = {}
+    for i in range(side * side):
+        a, b = abs(i % side - W), abs(i // side - W)
+        keys.setdefault((min(a, b), max(a, b)), []).append(i)
+    ks = sorted(keys)
+    return np.array([np.mean(P[keys[k]]) for k in ks]), ks
+
+
+def test_measured_feq_agrees_statistically_with_oracle(mdlg, orc):
+    """Tiny plain-MDLG workload (N=1024, phi=0.0784, T=20, dt=5e-4, FP64,
+    dt_lg=0.2, lattice 101x101, W=4): independent GPU and oracle trajectories
+    give the same equilibrium within statistical error (chi^2 over the 15
+    symmetric sets, p > 1e-3)."""
+    from scipy import stats
+
+    n, W, every, nsteps, neq = 1024, 4, 400, 20_000, 2000
+    L = inputs.box_length(n, 0.0784)
+    # GPU: 16 replicas with seeds 101.. in one batched system
+    reps = [inputs.lattice_gas_state(n, L, 20.0, seed=101 + r) for r in range(16)]
+    p = mdlg.make_params(n, L, precision=mdlg.MD_FP64, W=W, n_equil=neq, lg_every=(every,),
+                         lx=(101,), block_windows=1)
+    cat = [np.concatenate([getattr(s, f) for s in reps]) for f in ("x", "y", "vx", "vy")]
+    s = mdlg.System([p] * 16, *cat)
+    s.step(neq + nsteps)
+    Le = s.rep_info(0).L_eff
+    g_est = []
+    for r in range(16):
+        Pm, _, st = s.feq_measured(r, 0, 0)
+        assert st.n_windows == nsteps // every
+        g_est.append(_orbit_mean(Pm, W)[0])
+    g_est = np.array(g_est)
+    # oracle: 4 independent seeds, each in 10 blocks of 2,000 steps
+    o_est = []
+    for seed in range(4):
+        stt = inputs.lattice_gas_state(n, Le, 20.0, seed=1 + seed)
+        r = orc.md_run(stt.x, stt.y, stt.vx, stt.vy, Le, 5e-4, neq)
+        x, y, vx, vy = r["x"], r["y"], r["vx"], r["vy"]
+        for blk in range(10):
+            r = orc.md_run(x, y, vx, vy, Le, 5e-4, 2000, every=[every], lx=[101], W=W)
+            x, y, vx, vy = r["x"], r["y"], r["vx"], r["vy"]
+            o_est.append(_orbit_mean(r["hist"][0, 0] / (n * r["nwin"][0]), W)[0])
+    o_est = np.array(o_est)
+    gm, om = g_est.mean(0), o_est.mean(0)
+    gse = g_est.std(0, ddof=1) / math.sqrt(len(g_est))
+    ose = o_est.std(0, ddof=1) / math.sqrt(len(o_est))
+    keep = (gm > 1e-4) & (om > 1e-4)
+    z = (gm - om)[keep] / np.sqrt(gse ** 2 + ose ** 2)[keep]
+    chi2 = float(np.sum(z ** 2))
+    assert stats.chi2.sf(chi2, int(keep.sum())) > 1e-3, (chi2, z)
+    assert np.max(np.abs(z)) < 4.5
+    s.close()
+
+
+def test_wsg_closer_than_gaussian_in_paper_regime(mdlg):
+    """Sec. 5: at a^2 ~ 0.16 the WSG equilibrium is closer to the measured one
+    than the single Gaussian (KL divergence), node 0 is enhanced and the first
+    layer depressed relative to the Gaussian."""
+    n, W, every = 4096, 4, 2000
+    L = inputs.box_length(n, 0.0784)
+    R = 24
+    reps = [inputs.lattice_gas_state(n, L, 20.0, seed=500 + r) for r in range(R)]
+    # dt_lg = 1.0: mu2 ~ 9 sigma^2 -> dx ~ 7.5 gives a^2 ~ 0.16
+    lx = int(round(L / 7.5))
+    p = mdlg.make_params(n, L, precision=mdlg.MD_FP32_CELLOFF, W=W, n_equil=4000,
+                         lg_every=(every,), lx=(lx,))
+    cat = [np.concatenate([getattr(s, f) for s in reps]) for f in ("x", "y", "vx", "vy")]
+    s = mdlg.System([p] * R, *cat)
+    s.step(4000 + 20 * every)
+    s.sync()
+    acc = np.zeros((2 * W + 1) ** 2)
+    mu2 = mu4 = 0.0
+    for r in range(R):
+        Pm, _, st = s.feq_measured(r, 0, 0, symmetrize=True)
+        acc += Pm / R
+        mu2 += st.mu2 / R
+        mu4 += st.mu4 / R
+    dx = s.rep_info(0).dx_eff[0]
+    a2 = mu2 / dx ** 2
+    assert 0.08 < a2 < 0.3
+    lam, rc = mdlg.wsg_lambda(mu2, mu4)
+    lam = lam.item()
+    assert lam > 0.1
+    g = mdlg.feq_gaussian(a2, W=W)
+    w = mdlg.feq_wsg(a2, lam, W=W)
+    Pd = _dev(acc)
+    kg = mdlg.feq_compare(Pd, g).cpu().numpy()[1]
+    kw = mdlg.feq_compare(Pd, w).cpu().numpy()[1]
+    assert kw < kg, (kw, kg)
+    c = (2 * W + 1) ** 2 // 2
+    gn = g.cpu().numpy()
+    assert acc[c] / gn[c] > 1.0          # node 0 enhanced
+    assert acc[c + 1] / gn[c + 1] < 1.0  # first layer depressed
+    s.close()
