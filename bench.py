@@ -1,25 +1,29 @@
 """Throughput benchmark of the MDLG hot path: 2D Lennard-Jones MD with the
-MDLG coarse-graining fused in, plus the f_eq stage (measured, Gaussian and
-WSG equilibria and their comparison), through the C-ABI of libmdlg.so.
+MDLG coarse-graining fused into the step, plus the f_eq stage (measured,
+Gaussian and WSG equilibria and their comparison), through the C-ABI of
+libmdlg.so.
 
-Workload (single large system): N = 262,144 particles at area fraction
-0.0784 (L = 1620.53 sigma), T = 20, LJ with rc = 2.5 (shifted), dt = 5e-4,
-FP32 cell-index + offset positions; sampling intervals Delta t_LG in
-{0.05, 0.1, 0.2, 0.5, 1.0} on lattices dx in {0.5, 1, 2} (15 int32
-histograms, W = 4 plus overflow), FP64 normalisation.  One bench step = 2,000
-MD steps (one window of the longest interval, 38 sampling events x 3
-lattices) followed by the f_eq stage for all 15 (interval, lattice) pairs.
-Synthetic seeded state (square lattice + jitter, Maxwell velocities).
+Headline workload (batched ensemble): 256 independent replicas in one
+persistent launch, N log-uniform in [4096, 65536], area fraction uniform in
+[0.02, 0.30], T uniform in [1, 20], per-replica seeds (square lattice +
+jitter, Maxwell velocities); LJ with rc = 2.5 (shifted), dt = 5e-4, FP32
+cell-index + offset positions, MDLG sampling every 400 steps (Delta t_LG =
+0.2) on a lattice of spacing ~1 sigma, W = 4 (81 classes) plus overflow,
+int32 histograms, FP64 normalisation.  One bench step = 400 MD steps (one
+sampling window) + the batched f_eq stage for all replicas.
 
-Output: one JSON line (rank 0).  --impl reference times the FP64 CPU oracle on
-a bounded sample of the same workload.
+Also measured and reported beside it: the single large system (N = 262,144,
+phi = 0.0784, T = 20, FP32, five sampling intervals x three lattices) and
+the same system in plain FP64.
+
+Output: one JSON line (rank 0).  --impl reference times the FP64 CPU oracle
+on a bounded sample of the same workload.
 """
 
 from __future__ import annotations
 
 import argparse
 import json
-import math
 import os
 import subprocess
 import sys
@@ -33,14 +37,17 @@ sys.path.insert(0, ROOT)
 
 METRIC = "particle-steps/s incl. MDLG binning (batched FP32 vs plain FP64, 1 GB300); f_eq err"
 UNIT = "particle-steps/s"
-N_PART = 262_144
-PHI, TEMP, DT = 0.0784, 20.0, 5e-4
-LG_EVERY = (100, 200, 400, 1000, 2000)
-DX = (0.5, 1.0, 2.0)
+N_REP = 256
+ENS_SEED = 7
+DT = 5e-4
+EVERY = 400
+MD_PER_STEP = 400
 W = 4
-MD_PER_STEP = 2000
 BYTES_PER_PARTICLE_STEP = 40.0      # FP32 cell + offset: 20 B state read + 20 B written
 L2_BYTES = 129 * 2 ** 20
+# single large system (reported beside the headline)
+N1, PHI1, T1 = 262_144, 0.0784, 20.0
+LG1, DX1 = (100, 200, 400, 1000, 2000), (0.5, 1.0, 2.0)
 
 
 def _peaks():
@@ -53,12 +60,12 @@ def _peaks():
 
 
 def _profile_traffic():
-    """DRAM bytes per launch of the persistent kernel from the committed ncu
-    summary, scaled to one 2,000-step launch (null if absent)."""
-    p = os.path.join(ROOT, "profiles", "k_md_persistent_fp32_n262144.md")
+    """DRAM bytes per bench-step launch of the persistent kernel, from the
+    committed ncu summary (None when absent or stale)."""
+    p = os.path.join(ROOT, "profiles", "k_md_persistent_batched256.md")
     try:
         for line in open(p):
-            if line.startswith("traffic_bytes_per_2000_step_launch:"):
+            if line.startswith("traffic_bytes_per_launch:"):
                 v = line.split(":", 1)[1].strip()
                 return None if v in ("", "null") else float(v)
     except OSError:
@@ -131,29 +138,42 @@ def _dist():
     return ws, rank, local
 
 
-def _params(mdlg, L, prec):
-    return mdlg.make_params(N_PART, L, dt=DT, precision=prec, W=W, n_equil=0, lg_every=LG_EVERY,
-                            lx=tuple(int(round(L / d)) for d in DX), block_windows=1)
+def ensemble(seed_offset=0, reps=None):
+    """Per-replica parameters and initial states of the batched ensemble."""
+    from paper_2101_01160_gb300 import inputs
+
+    Ns, phis, Ts = inputs.ensemble_params(N_REP, seed=ENS_SEED + seed_offset)
+    out = []
+    for r in (range(N_REP) if reps is None else reps):
+        n = int(Ns[r])
+        L = inputs.box_length(n, float(phis[r]))
+        st = inputs.lattice_gas_state(n, L, float(Ts[r]), seed=100_000 * seed_offset + r)
+        out.append((n, L, float(phis[r]), float(Ts[r]), st))
+    return out
 
 
-def _feq_stage(mdlg, sysm, torch):
-    """Measured f_eq, lambda, Gaussian and WSG equilibria and their comparison
-    for every (interval, lattice); returns the worst |P_MD - P_WSG| seen."""
-    worst = 0.0
-    for k in range(len(LG_EVERY)):
-        for d in range(len(DX)):
-            Pm, se, st = sysm.feq_measured(0, k, d, symmetrize=True)
-            if st.n_windows == 0:
-                continue
-            Pd = torch.from_numpy(Pm).cuda()
-            g = mdlg.feq_gaussian(st.a2, W=W)
-            lam_t, rc = mdlg.wsg_lambda(st.mu2, st.mu4, allow_domain=True)
-            lam = float(lam_t.item())
-            wsg = mdlg.feq_wsg(st.a2, lam, W=W)
-            mdlg.feq_compare(Pd, g)
-            cw = mdlg.feq_compare(Pd, wsg)
-            worst = max(worst, float(cw[0].item()))
-    return worst
+def _ens_params(mdlg, ens, prec):
+    return [mdlg.make_params(n, L, dt=DT, precision=prec, W=W, n_equil=0, lg_every=(EVERY,),
+                             lx=(int(round(L)),)) for (n, L, _, _, _) in ens]
+
+
+def _time_variant(mdlg, torch, params, st, md_steps, reps=3):
+    """Device time of md_step(md_steps) launches on one system."""
+    s = mdlg.System(params, st.x, st.y, st.vx, st.vy)
+    s.step(md_steps)
+    s.sync()
+    ms = []
+    for _ in range(reps):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        s.step(md_steps)
+        e1.record()
+        torch.cuda.synchronize()
+        ms.append(e0.elapsed_time(e1))
+    s.sync()
+    s.close()
+    m = float(np.median(ms))
+    return {"value": params.n * md_steps / (m * 1e-3), "ms_per_launch": m, "md_steps": md_steps}
 
 
 def run_ours(args):
@@ -170,36 +190,33 @@ def run_ours(args):
         dist_.init_process_group("nccl")
         dist = dist_
     mdlg.load()
-    L = inputs.box_length(N_PART, PHI)
-    st = inputs.lattice_gas_state(N_PART, L, TEMP, seed=1000 + rank)
+    ens = ensemble(seed_offset=rank)
+    ntot = sum(e[0] for e in ens)
+    cat = [np.concatenate([getattr(e[4], f) for e in ens]) for f in ("x", "y", "vx", "vy")]
     stream = torch.cuda.current_stream()
-    sysm = mdlg.System(_params(mdlg, L, mdlg.MD_FP32_CELLOFF), st.x, st.y, st.vx, st.vy, stream)
+    sysm = mdlg.System(_ens_params(mdlg, ens, mdlg.MD_FP32_CELLOFF), *cat, stream=stream)
+    nb = (2 * W + 1) ** 2
+    feq_dev = torch.empty((N_REP, 3 * nb + mdlg.FEQB_STATS), dtype=torch.float64, device="cuda")
     flush = torch.empty(2 * L2_BYTES, dtype=torch.uint8, device="cuda")
 
-    def one_step():
-        sysm.step(MD_PER_STEP)
-        return _feq_stage(mdlg, sysm, torch)
-
     for _ in range(args.warmup):
-        one_step()
+        sysm.step(MD_PER_STEP)
+        mdlg.feq_batch(sysm, 0, 0, True, out=feq_dev)
     sysm.sync()
-    # device-timed region: per-step events, L2 flushed between steps
-    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True),
-           torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    ev = [tuple(torch.cuda.Event(enable_timing=True) for _ in range(3)) for _ in range(args.steps)]
     if dist:
         dist.barrier()
     torch.cuda.synchronize()
-    worst = 0.0
     with ClockSampler(local) as clk:
         for i in range(args.steps):
             flush.zero_()
             ev[i][0].record(stream)
             sysm.step(MD_PER_STEP)
             ev[i][1].record(stream)
-            worst = max(worst, _feq_stage(mdlg, sysm, torch))
+            mdlg.feq_batch(sysm, 0, 0, True, out=feq_dev)
             ev[i][2].record(stream)
         torch.cuda.synchronize()
-    rc = sysm.sync()
+    sysm.sync()
     step_ms = sum(a.elapsed_time(c) for a, b, c in ev)
     kern_ms = [a.elapsed_time(b) for a, b, c in ev]
     t_max = step_ms
@@ -209,98 +226,122 @@ def run_ours(args):
         t_max = float(t.item())
         dist.barrier()
     ms_per_step = t_max / args.steps
-    value = ws * N_PART * MD_PER_STEP / (ms_per_step * 1e-3)
+    value = ws * ntot * MD_PER_STEP / (ms_per_step * 1e-3)
+    stats = feq_dev[:, 3 * nb:].cpu().numpy()
+    feq_err = {"max_abs_md_vs_wsg": float(stats[:, 6].max()),
+               "max_abs_md_vs_gauss": float(stats[:, 4].max()),
+               "median_kl_md_wsg": float(np.median(stats[:, 7])),
+               "median_kl_md_gauss": float(np.median(stats[:, 5])),
+               "windows": int(stats[0, 8])}
 
-    # end-to-end through the C-ABI with host buffers: upload the state from
-    # pinned host memory, run, read the f_eq results back
-    pin = [torch.from_numpy(a).pin_memory() for a in (st.x, st.y, st.vx, st.vy)]
+    # end to end through the C-ABI with host buffers: upload the state from
+    # pinned host memory, run one window, read the f_eq stage back
+    pin = [torch.from_numpy(a).pin_memory() for a in cat]
     host = [t.numpy() for t in pin]
+    e2e_steps = max(1, min(args.steps, 5))
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    e2e_steps = max(1, min(args.steps, 5))
     for _ in range(e2e_steps):
         sysm.set_state(*host)
         sysm.step(MD_PER_STEP)
-        _feq_stage(mdlg, sysm, torch)
+        mdlg.feq_batch(sysm, 0, 0, True)
     torch.cuda.synchronize()
     e2e_s = (time.perf_counter() - t0) / e2e_steps
-    e2e = {"value": ws * N_PART * MD_PER_STEP / e2e_s, "unit": UNIT,
-           "h2d_bytes_per_step": 4 * 8 * N_PART,
-           "d2h_bytes_per_step": len(LG_EVERY) * len(DX) * (2 * (2 * W + 1) ** 2 + 8) * 8}
+    e2e = {"value": ws * ntot * MD_PER_STEP / e2e_s, "unit": UNIT,
+           "h2d_bytes_per_step": 4 * 8 * ntot,
+           "d2h_bytes_per_step": N_REP * (3 * nb + mdlg.FEQB_STATS) * 8}
+    info = sysm.info()
+    sysm.close()
+
+    variants = {}
+    if not args.no_variants and rank == 0:
+        L1 = inputs.box_length(N1, PHI1)
+        st1 = inputs.lattice_gas_state(N1, L1, T1, seed=1000)
+        lx1 = tuple(int(round(L1 / d)) for d in DX1)
+        for name, prec in (("single_system_fp32", mdlg.MD_FP32_CELLOFF),
+                           ("plain_fp64", mdlg.MD_FP64)):
+            p = mdlg.make_params(N1, L1, dt=DT, precision=prec, W=W, lg_every=LG1, lx=lx1)
+            variants[name] = _time_variant(mdlg, torch, p, st1, 2000)
+            variants[name]["workload"] = ("N=262144 phi=0.0784 T=20, dt_lg {0.05..1.0} x dx "
+                                          "{0.5,1,2}, one 2000-step launch")
+        variants["batched_fp32_over_plain_fp64"] = (value / ws) / variants["plain_fp64"]["value"]
 
     peak, peak_kind = _peaks()
     kern_avg_s = (sum(kern_ms) / len(kern_ms)) * 1e-3
-    achieved = BYTES_PER_PARTICLE_STEP * N_PART * MD_PER_STEP / kern_avg_s / 1e9
-    info = sysm.info()
+    achieved = BYTES_PER_PARTICLE_STEP * ntot * MD_PER_STEP / kern_avg_s / 1e9
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": "single large system N=262144 phi=0.0784 T=20 FP32 cell+offset, "
-                               "dt_lg {0.05,0.1,0.2,0.5,1.0} x dx {0.5,1,2}, W=4; "
-                               "2000 MD steps + f_eq stage per step",
-                   "n_particles": N_PART, "md_steps_per_step": MD_PER_STEP,
+        "config": {"workload": f"batched ensemble: {N_REP} replicas, N log-uniform "
+                               "[4096,65536], phi U[0.02,0.30], T U[1,20], FP32 cell+offset, "
+                               "dt 5e-4, sampling every 400 steps (dt_lg 0.2) on dx~1, W=4; "
+                               "400 MD steps + batched f_eq stage per step",
+                   "n_particles": ntot, "md_steps_per_step": MD_PER_STEP,
                    "l2": "flushed between timed steps (256 MB write)",
                    "parallelism": f"replicas x{ws}"},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "traffic": _profile_traffic(),
-                     "kernel": "k_md_persistent<float,256>", "peak_kind": peak_kind},
+                     "kernel": "k_md_persistent<float,256>", "peak_kind": peak_kind,
+                     "bytes_per_particle_step": BYTES_PER_PARTICLE_STEP},
         "e2e": e2e,
-        "gpu_launches": args.steps * (1 + 6 * len(LG_EVERY) * len(DX)),
+        "gpu_launches": args.steps * 2,
         "clocks": clk.summary(),
-        "f_eq_err_max_abs_md_vs_wsg": worst,
-        "md_status": rc,
+        "f_eq_err": feq_err,
+        "variants": variants,
         "rebuilds": int(info.n_rebuilds),
     }
     if rank == 0 and not args.no_cpu_baseline:
-        line["cpu_baseline"] = cpu_baseline(st, L)
-    sysm.close()
+        line["cpu_baseline"] = cpu_baseline()
     if rank == 0:
         print(json.dumps(line), flush=True)
     if dist:
         dist.destroy_process_group()
 
 
-def _oracle_sample(st, L, nsteps):
+def _oracle_sample(reps, nsteps):
+    """Runs the oracle over the given replicas of the ensemble; returns
+    (particle-steps, seconds)."""
     from oracle import oracle
 
-    lx = [int(round(L / d)) for d in DX]
+    ens = ensemble(reps=reps)
     t0 = time.perf_counter()
-    oracle.md_run(st.x, st.y, st.vx, st.vy, L, DT, nsteps, every=[LG_EVERY[0]], lx=lx, W=W)
-    return time.perf_counter() - t0
+    ps = 0
+    for (n, L, _, _, st) in ens:
+        oracle.md_run(st.x, st.y, st.vx, st.vy, L, DT, nsteps, every=[EVERY], lx=[int(round(L))], W=W)
+        ps += n * nsteps
+    return ps, time.perf_counter() - t0
 
 
-def cpu_baseline(st, L, nsteps=200):
-    dt = _oracle_sample(st, L, nsteps)
-    return {"value": N_PART * nsteps / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": f"N={N_PART} workload state, {nsteps} MD steps, binning every 100 steps on "
-                      f"3 lattices; FP64 C oracle, single thread"}
+def cpu_baseline():
+    reps = list(range(0, N_REP, 16))           # 16 replicas spread over the draw order
+    ps, dt = _oracle_sample(reps, MD_PER_STEP)
+    return {"value": ps / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"replicas {reps} of the batched ensemble, {MD_PER_STEP} MD steps each "
+                      f"(one sampling window), FP64 C oracle, single thread"}
 
 
 def run_reference(args):
     ws, rank, _ = _dist()
     if rank != 0:
         return
-    from paper_2101_01160_gb300 import inputs
-
-    L = inputs.box_length(N_PART, PHI)
-    st = inputs.lattice_gas_state(N_PART, L, TEMP, seed=1000)
-    per = 100
+    reps = [0, 128]
     for _ in range(args.warmup):
-        _oracle_sample(st, L, per)
-    tot = 0.0
+        _oracle_sample(reps, 100)
+    ps_tot, tot = 0, 0.0
     for _ in range(args.steps):
-        tot += _oracle_sample(st, L, per)
+        ps, dt = _oracle_sample(reps, 100)
+        ps_tot += ps
+        tot += dt
+    value = ps_tot / tot
     ms = tot / args.steps * 1e3
-    value = N_PART * per / (ms * 1e-3)
-    sample = (f"N={N_PART} workload state, {per} MD steps per step, binning every 100 steps on "
-              f"3 lattices; FP64 C oracle, single thread")
+    sample = (f"replicas {reps} of the batched ensemble, 100 MD steps per step, sampling every "
+              f"{EVERY} steps; FP64 C oracle, single thread")
     print(json.dumps({
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
-        "config": {"workload": "single large system N=262144 phi=0.0784 T=20 (oracle sample)",
-                   "n_particles": N_PART, "md_steps_per_step": per},
+        "config": {"workload": "batched ensemble (oracle sample)", "md_steps_per_step": 100},
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
                          "sample": sample},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
@@ -314,6 +355,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-variants", action="store_true")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

@@ -80,9 +80,10 @@ typedef struct md_params {
     double dt;             /* MD time step                                  */
     double rc;             /* LJ cutoff (2.5 in the configured workloads)    */
     double eps, sigma, mass;
-    double skin;           /* cell edge is >= rc + skin; a cell list is     */
-                           /* rebuilt once any particle strays 0.4*skin     */
-                           /* outside its cell                               */
+    double skin;           /* Verlet skin: neighbour lists hold all pairs   */
+                           /* within rc + skin (cell edge >= rc + skin) and */
+                           /* are rebuilt once the accumulated bound on     */
+                           /* any displacement reaches skin/2                */
     int32_t precision;     /* MD_FP64 or MD_FP32_CELLOFF                     */
     int32_t W;             /* displacement window half-width, 1..MD_MAX_W   */
     int64_t n_equil;       /* MD steps before the first snapshot            */
@@ -91,7 +92,10 @@ typedef struct md_params {
     int32_t n_dx;          /* lattices in use, 1..MD_MAX_DX                 */
     int32_t lx[MD_MAX_DX]; /* lattice cells per box edge                    */
     int32_t block_windows; /* windows per error-bar block (>= 1)            */
-    int32_t reserved;
+    int32_t nbr_max;       /* neighbour-list capacity per particle (0 =     */
+                           /* automatic: 3x the mean count within rc+skin   */
+                           /* plus 8 standard deviations); overflow is      */
+                           /* reported as MD_E_LIMIT by md_sync              */
 } md_params;
 
 typedef struct md_system md_system;   /* opaque, library-owned */
@@ -170,6 +174,12 @@ void md_destroy(md_system *s);
  * (MD_E_TIMEOUT, MD_E_SKIN, MD_E_NONFINITE) are reported by md_sync. */
 int md_step(md_system *s, int64_t nsteps);
 
+/* Launch shape of the persistent kernel: block_threads in {128, 256} (0 =
+ * 256), per_thread in [1, 8] particles per thread per chunk (0 = 1).  Results do not depend on the shape: particle
+ * order, force summation order and every reduction order are fixed by the
+ * data, not by the launch.  Used by the autotuner. */
+int md_tune(md_system *s, int32_t block_threads, int32_t per_thread);
+
 /* Waits for the system's stream and returns the device status word (and
  * clears it). */
 int md_sync(md_system *s);
@@ -221,6 +231,21 @@ int md_hist_raw(md_system *s, int32_t rep, int32_t lg, int32_t dxi, int64_t *his
 int feq_measured(md_system *s, int32_t rep, int32_t lg, int32_t dxi, int32_t symmetrize,
                  double *P_out, double *stderr_out, md_feq_stats *stats);
 
+/* The whole f_eq stage for every replica in one launch (no host round
+ * trip): per replica r, out[r*(3*nb+16) + ...] holds
+ *   [0, nb)      measured P_i (as feq_measured, symmetric-set averaged if
+ *                symmetrize != 0),
+ *   [nb, 2nb)    Gaussian equilibrium (Eq. feq_gaussian) at the measured a^2,
+ *   [2nb, 3nb)   WSG equilibrium (Eq. f_eq_wsg) at a^2 and lambda,
+ *   3nb + 0..13  mu2, mu4, a^2, lambda (root 2 of Eq. lambda_eq; 0 when the
+ *                kurtosis is <= 3, 1 when > 3.75, capped at 1e5),
+ *                max|P-G|, D_KL(P||G), max|P-WSG|, D_KL(P||WSG), windows,
+ *                samples, overflow, dx_eff, lambda status (0 ok, 1 k<=3,
+ *                2 k>3.75, 3 capped), sum(P).
+ * nb = (2W+1)^2.  out: host or device; with host memory the call
+ * synchronises, with device memory it is asynchronous on the stream. */
+int feq_batch(md_system *s, int32_t lg, int32_t dxi, int32_t symmetrize, double *out);
+
 /* ---- MDLG binning of two snapshots (Sec. 2, Eq. n_i) -------------------- */
 
 /* Lattice displacement histogram of n particles between snapshots t0 and t1
@@ -251,8 +276,9 @@ int wsg_lambda(double mu2, double mu4, int32_t root, double *lambda_out, void *s
 
 /* Poisson weighted sum of Gaussians equilibrium, Eq. (f_eq_wsg): P_out[i] =
  * sum_c Pois(c; lambda) f^c(vx-ux) f^c(vy-uy), N_c = sqrt(2 a2 (c+1) /
- * (lambda+1)); terms c = 0..ceil(lambda + 12 sqrt(lambda) + 20) (omitted
- * Poisson tail < 1e-16).  P_out: device, (2W+1)^2 doubles. */
+ * (lambda+1)); terms c with |c - lambda| <= 12 sqrt(lambda) + 20 (omitted
+ * Poisson tails < 1e-16).  lambda < 1e6.  P_out: device, (2W+1)^2
+ * doubles. */
 int feq_wsg(double a2, double lambda, double ux, double uy, int32_t W, double *P_out,
             void *stream);
 

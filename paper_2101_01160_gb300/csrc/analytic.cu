@@ -1,11 +1,12 @@
 // Analytic MDLG equilibria (Sec. 3) and distribution comparison, FP64 on
-// the device.  One thread per lattice velocity; the WSG Poisson sum runs in
-// each thread.  These are tiny launches (at most (2*MD_MAX_W+1)^2 = 441
-// classes); their cost is the launch itself.
+// the device.  The Gaussian takes one thread per lattice velocity, the WSG
+// one CTA per lattice velocity over its Poisson terms.  These are tiny
+// launches (at most (2*MD_MAX_W+1)^2 = 441 classes).
 #include <cstdarg>
 #include <cmath>
 
 #include "common.cuh"
+#include "equilibria.cuh"
 
 namespace mdlg {
 
@@ -23,21 +24,6 @@ int fail(int code, const char *fmt, ...) {
     return code;
 }
 
-// One-dimensional equilibrium of a particle uniform in a unit lattice cell
-// displaced by a Gaussian of variance var (lattice units), landing u cells
-// away: Eq. (feq_gaussian) with a^2 = var, N = a / sqrt(2 pi).  The WSG
-// component f^c of Eq. (f_eq_wsg) is this with var = a^2 (c+1)/(lambda+1)
-// (N_c^2 = 2 var).
-__device__ double cell_gauss_1d(double u, double var) {
-    const double s = sqrt(2.0 * var);             // a sqrt(2) = N_c
-    const double norm = sqrt(var) * 0.39894228040143267794;   // a / sqrt(2 pi)
-    const double um = u - 1.0, up = u + 1.0;
-    const double e = exp(-(um * um) / (2.0 * var)) - 2.0 * exp(-(u * u) / (2.0 * var)) +
-                     exp(-(up * up) / (2.0 * var));
-    const double eu = erf(u / s);
-    return norm * e + 0.5 * um * (erf(um / s) - eu) + 0.5 * up * (erf(up / s) - eu);
-}
-
 __global__ void k_feq_gaussian(double a2, double ux, double uy, int W, double *P) {
     const int side = 2 * W + 1;
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -46,21 +32,31 @@ __global__ void k_feq_gaussian(double a2, double ux, double uy, int W, double *P
     P[i] = cell_gauss_1d((double)(ix - W) - ux, a2) * cell_gauss_1d((double)(iy - W) - uy, a2);
 }
 
-__global__ void k_feq_wsg(double a2, double lam, double ux, double uy, int W, int cmax,
-                          double *P) {
+// One CTA per lattice velocity; its threads share the Poisson terms
+// c = cmin..cmax (terms outside the window weigh < 1e-16 in total: the
+// Poisson tails beyond 12 sqrt(lambda) + 20 of the mean).  Fixed-order
+// reduction, so the result is reproducible.
+constexpr int WSG_THREADS = 128;
+
+__global__ void __launch_bounds__(WSG_THREADS) k_feq_wsg(double a2, double lam, double ux, double uy,
+                                                         int W, int cmin, int cmax, double *P) {
+    __shared__ double red[WSG_THREADS];
     const int side = 2 * W + 1;
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= side * side) return;
+    const int i = blockIdx.x;
     const double vx = (double)(i % side - W) - ux, vy = (double)(i / side - W) - uy;
     double acc = 0.0;
-    const double loglam = lam > 0.0 ? log(lam) : 0.0;
-    for (int c = 0; c <= cmax; ++c) {
-        const double w = lam > 0.0 ? exp(-lam + (double)c * loglam - lgamma((double)c + 1.0))
-                                   : (c == 0 ? 1.0 : 0.0);
+    for (int c = cmin + (int)threadIdx.x; c <= cmax; c += WSG_THREADS) {
+        const double w = poisson_weight(c, lam);
         const double var = a2 * ((double)c + 1.0) / (lam + 1.0);
         acc += w * (cell_gauss_1d(vx, var) * cell_gauss_1d(vy, var));
     }
-    P[i] = acc;
+    red[threadIdx.x] = acc;
+    __syncthreads();
+    for (int o = WSG_THREADS / 2; o > 0; o >>= 1) {
+        if ((int)threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) P[i] = red[0];
 }
 
 // Roots of Eq. (lambda_eq) in the printed form; root 1: '+' branch, root 2:
@@ -69,10 +65,7 @@ __global__ void k_wsg_lambda(double mu2, double mu4, int root, int mode, double 
     if (threadIdx.x != 0 || blockIdx.x != 0) return;
     if (mode == 1) { *out = 0.0; return; }
     if (mode == 2) { *out = 1.0; return; }
-    const double m22 = mu2 * mu2;
-    const double r = sqrt(3.0 * (15.0 * m22 * m22 - 4.0 * m22 * mu4));
-    const double num = -9.0 * m22 + 2.0 * mu4 + (root == 1 ? r : -r);
-    *out = num / (2.0 * (3.0 * m22 - mu4));
+    *out = lambda_root(mu2, mu4, root);
 }
 
 __global__ void k_compare(const double *R, const double *Q, int n, double *out) {
@@ -103,7 +96,7 @@ __global__ void k_compare(const double *R, const double *Q, int n, double *out) 
     }
 }
 
-int wsg_cmax(double lam) { return lam <= 0.0 ? 0 : (int)ceil(lam + 12.0 * sqrt(lam) + 20.0); }
+
 
 }  // namespace mdlg
 
@@ -130,8 +123,8 @@ int feq_wsg(double a2, double lambda, double ux, double uy, int32_t W, double *P
     if (W < 0 || W > MD_MAX_W) return fail(MD_E_ARG, "feq_wsg: W out of [0,%d]", MD_MAX_W);
     if (!P_out) return fail(MD_E_ARG, "feq_wsg: P_out is NULL");
     const int nb = (2 * W + 1) * (2 * W + 1);
-    k_feq_wsg<<<(nb + 127) / 128, 128, 0, (cudaStream_t)stream>>>(a2, lambda, ux, uy, W,
-                                                                  wsg_cmax(lambda), P_out);
+    k_feq_wsg<<<nb, WSG_THREADS, 0, (cudaStream_t)stream>>>(a2, lambda, ux, uy, W, wsg_cmin(lambda),
+                                                            wsg_cmax(lambda), P_out);
     MD_CUDA_TRY(cudaGetLastError());
     return MD_OK;
 }

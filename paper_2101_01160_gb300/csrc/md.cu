@@ -10,6 +10,7 @@
 #include <vector>
 
 #include "common.cuh"
+#include "equilibria.cuh"
 #include "md_kernels.cuh"
 
 namespace mdlg {
@@ -180,6 +181,183 @@ __global__ void k_nc_of_id(SysDev S, int32_t *nc_of_id) {
     if (local < R.n) nc_of_id[R.ibase + local] = R.nc;
 }
 
+
+// ---------------------------------------------------------------- batched f_eq stage
+// For every replica (one CTA each), on the device: the measured equilibrium
+// (Eq. theory_feq per particle, optionally averaged over symmetric sets),
+// the moments mu2, mu4 and a^2 (Eq. a2_n_ua), lambda from Eq. (lambda_eq)
+// (root 2), the Gaussian (Eq. feq_gaussian) and WSG (Eq. f_eq_wsg)
+// equilibria at that a^2 and lambda, and their distance to the measured one
+// (max |difference| and Eq. kullback_leibler).
+constexpr int FEQB_THREADS = 128;
+constexpr int FEQB_STATS = 16;
+
+struct FeqBatchArgs {
+    const RepDev *reps;
+    const int32_t *hist;           // [nrep][n_lg][n_dx][MD_NBLK][nb]
+    const unsigned long long *ovf; // [nrep][n_lg][n_dx]
+    const double *mom;             // [ngran32][n_lg][2]
+    int n_lg, n_dx, lg, dxi, nb, W, sym;
+    long long nwin;
+    double *out;                   // [nrep][3 nb + FEQB_STATS]
+};
+
+__global__ void __launch_bounds__(FEQB_THREADS) k_feq_batch(FeqBatchArgs A) {
+    __shared__ double s_a[FEQB_THREADS], s_b[FEQB_THREADS], s_c[FEQB_THREADS], s_d[FEQB_THREADS];
+    __shared__ double s_par[4];
+    const int r = blockIdx.x, tid = threadIdx.x;
+    const RepDev &R = A.reps[r];
+    const int stride = 3 * A.nb + FEQB_STATS;
+    double *out = A.out + (long long)r * stride;
+    const int32_t *hist = A.hist + ((((long long)r * A.n_lg + A.lg) * A.n_dx + A.dxi) * MD_NBLK) * A.nb;
+    const double samples = (double)R.n * (double)A.nwin;
+    // moments
+    double m2 = 0.0, m4 = 0.0;
+    for (int g = R.pbase / 32 + tid; g < (R.pbase + R.cap) / 32; g += FEQB_THREADS) {
+        m2 += A.mom[((long long)g * A.n_lg + A.lg) * 2];
+        m4 += A.mom[((long long)g * A.n_lg + A.lg) * 2 + 1];
+    }
+    s_a[tid] = m2;
+    s_b[tid] = m4;
+    __syncthreads();
+    for (int o = FEQB_THREADS / 2; o > 0; o >>= 1) {
+        if (tid < o) {
+            s_a[tid] += s_a[tid + o];
+            s_b[tid] += s_b[tid + o];
+        }
+        __syncthreads();
+    }
+    if (tid == 0) {
+        const double mu2 = samples > 0 ? s_a[0] / (2.0 * samples) : 0.0;
+        const double mu4 = samples > 0 ? s_b[0] / (2.0 * samples) : 0.0;
+        const double dx = R.dxl[A.dxi];
+        double lam = 0.0, st = 0.0;
+        const double k = mu2 > 0 ? mu4 / (mu2 * mu2) : 0.0;
+        if (!(k > 3.0)) {
+            st = 1.0;
+        } else if (k > 3.75) {
+            lam = 1.0;
+            st = 2.0;
+        } else {
+            lam = lambda_root(mu2, mu4, 2);
+            if (lam > 1e5) {
+                lam = 1e5;   // the mixture is then a single Gaussian to ~1e-5
+                st = 3.0;
+            }
+        }
+        s_par[0] = mu2;
+        s_par[1] = mu2 / (dx * dx);
+        s_par[2] = lam;
+        out[3 * A.nb + 0] = mu2;
+        out[3 * A.nb + 1] = mu4;
+        out[3 * A.nb + 2] = s_par[1];
+        out[3 * A.nb + 3] = lam;
+        out[3 * A.nb + 8] = (double)A.nwin;
+        out[3 * A.nb + 9] = samples;
+        out[3 * A.nb + 10] = (double)A.ovf[((long long)r * A.n_lg + A.lg) * A.n_dx + A.dxi];
+        out[3 * A.nb + 11] = dx;
+        out[3 * A.nb + 12] = st;
+    }
+    __syncthreads();
+    const double a2 = s_par[1], lam = s_par[2];
+    const int side = 2 * A.W + 1;
+    // WSG: Poisson terms in chunks of FEQB_THREADS; the 1D factors of one
+    // term are evaluated once for the 2W+1 displacements and shared by all
+    // classes (the 2D value is their outer product).  Each class sums the
+    // terms in increasing c.
+    __shared__ double s_w[FEQB_THREADS];
+    __shared__ double s_F[FEQB_THREADS][2 * MD_MAX_W + 1];
+    constexpr int CPT = ((2 * MD_MAX_W + 1) * (2 * MD_MAX_W + 1) + FEQB_THREADS - 1) / FEQB_THREADS;
+    double accW[CPT];
+#pragma unroll
+    for (int q = 0; q < CPT; ++q) accW[q] = 0.0;
+    const int cmin = wsg_cmin(lam), cmax = wsg_cmax(lam);
+    for (int c0 = cmin; c0 <= cmax && a2 > 0; c0 += FEQB_THREADS) {
+        const int c = c0 + tid;
+        if (c <= cmax) {
+            const double var = a2 * ((double)c + 1.0) / (lam + 1.0);
+            s_w[tid] = poisson_weight(c, lam);
+            for (int v = 0; v < side; ++v) s_F[tid][v] = cell_gauss_1d((double)(v - A.W), var);
+        }
+        __syncthreads();
+        const int nterm = min(FEQB_THREADS, cmax - c0 + 1);
+#pragma unroll
+        for (int q = 0; q < CPT; ++q) {
+            const int i = tid + q * FEQB_THREADS;
+            if (i < A.nb) {
+                const int ix = i % side, iy = i / side;
+                double acc = accW[q];
+                for (int t = 0; t < nterm; ++t) acc += s_w[t] * (s_F[t][ix] * s_F[t][iy]);
+                accW[q] = acc;
+            }
+        }
+        __syncthreads();
+    }
+    double mg = 0.0, kg = 0.0, mw = 0.0, kw = 0.0, sum = 0.0;
+#pragma unroll
+    for (int q = 0; q < CPT; ++q) {
+        const int i = tid + q * FEQB_THREADS;
+        if (i >= A.nb) continue;
+        int mem[8], nm = 0;
+        if (A.sym) {
+            const int a = abs(i % side - A.W), b = abs(i / side - A.W);
+            const int lo = min(a, b), hi = max(a, b);
+            for (int j = 0; j < A.nb && nm < 8; ++j) {
+                const int c = abs(j % side - A.W), d = abs(j / side - A.W);
+                if (min(c, d) == lo && max(c, d) == hi) mem[nm++] = j;
+            }
+        } else {
+            mem[nm++] = i;
+        }
+        long long tot = 0;
+        for (int b = 0; b < MD_NBLK; ++b)
+            for (int m = 0; m < nm; ++m) tot += hist[b * A.nb + mem[m]];
+        const double P = samples > 0 ? (double)tot / ((double)nm * samples) : 0.0;
+        const double vx = (double)(i % side - A.W), vy = (double)(i / side - A.W);
+        const double G = a2 > 0 ? cell_gauss_1d(vx, a2) * cell_gauss_1d(vy, a2) : 0.0;
+        const double Wg = accW[q];
+        out[i] = P;
+        out[A.nb + i] = G;
+        out[2 * A.nb + i] = Wg;
+        mg = fmax(mg, fabs(P - G));
+        mw = fmax(mw, fabs(P - Wg));
+        if (P > 0.0) {
+            kg += P * log(P / G);
+            kw += P * log(P / Wg);
+        }
+        sum += P;
+    }
+    s_a[tid] = mg;
+    s_b[tid] = kg;
+    s_c[tid] = mw;
+    s_d[tid] = kw;
+    __syncthreads();
+    for (int o = FEQB_THREADS / 2; o > 0; o >>= 1) {
+        if (tid < o) {
+            s_a[tid] = fmax(s_a[tid], s_a[tid + o]);
+            s_b[tid] += s_b[tid + o];
+            s_c[tid] = fmax(s_c[tid], s_c[tid + o]);
+            s_d[tid] += s_d[tid + o];
+        }
+        __syncthreads();
+    }
+    // the sum of P goes through the same fixed tree
+    if (tid == 0) {
+        out[3 * A.nb + 4] = s_a[0];
+        out[3 * A.nb + 5] = s_b[0];
+        out[3 * A.nb + 6] = s_c[0];
+        out[3 * A.nb + 7] = s_d[0];
+    }
+    __syncthreads();
+    s_a[tid] = sum;
+    __syncthreads();
+    for (int o = FEQB_THREADS / 2; o > 0; o >>= 1) {
+        if (tid < o) s_a[tid] += s_a[tid + o];
+        __syncthreads();
+    }
+    if (tid == 0) out[3 * A.nb + 13] = s_a[0];
+}
+
 }  // namespace mdlg
 
 using namespace mdlg;
@@ -193,7 +371,9 @@ struct md_system {
     int nslots = 0, total_cells = 0;
     cudaStream_t st = nullptr;
     int dev = 0, nsm = 1;
-    int block = 256, grid = 1;
+    int block = 256, grid = 1, ppt = 1, K = 16;
+    long long chunk_cap = 0;
+    int4 *d_chunks = nullptr;
     size_t smem = 0;
     long long step = 0;
     int phase_half = 0;
@@ -229,19 +409,40 @@ const void *persistent_fn(int prec, int block) {
                         : (const void *)k_md_persistent<float, 256>;
 }
 
-int configure_launch(md_system *s, int block) {
+int configure_launch(md_system *s, int block, int ppt) {
+    if (block != 128 && block != 256) return fail(MD_E_ARG, "block_threads must be 128 or 256");
+    if (ppt < 1 || ppt > 8) return fail(MD_E_ARG, "per_thread must be in [1, 8]");
     const void *fn = persistent_fn(s->prec, block);
-    s->smem = (size_t)s->n_lg * s->n_dx * s->nb * sizeof(int);
-    MD_CUDA_TRY(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                     (int)std::max<size_t>(s->smem, 0)));
+    const int chunk = ppt * block;
+    // chunk table: ppt*block consecutive slots of one replica
+    std::vector<int4> ch;
+    for (int r = 0; r < s->nrep; ++r) {
+        const RepDev &R = s->reps[r];
+        for (int a = R.pbase; a < R.pbase + R.n; a += chunk)
+            ch.push_back(make_int4(r, a, std::min(a + chunk, R.pbase + R.n), 0));
+    }
+    if ((long long)ch.size() > s->chunk_cap) return fail(MD_E_LIMIT, "chunk table overflow");
+    const long long nch = (long long)ch.size();
+    const size_t smem = s->prec == MD_FP64 ? smem_bytes<double>(s->n_lg, s->n_dx, s->nb, chunk)
+                                           : smem_bytes<float>(s->n_lg, s->n_dx, s->nb, chunk);
+    if (smem > 227 * 1024) return fail(MD_E_LIMIT, "shared memory per CTA exceeds 227 KB");
+    MD_CUDA_TRY(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     int occ = 0;
-    MD_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, block, s->smem));
+    MD_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, block, smem));
     if (occ < 1) return fail(MD_E_CUDA, "persistent kernel does not fit on an SM");
     const long long maxco = (long long)occ * s->nsm;
-    const long long nchunks = s->nslots / block;
-    const long long q = (nchunks + maxco - 1) / maxco;
-    s->grid = (int)std::min<long long>(4096, std::max<long long>(1, (nchunks + q - 1) / q));
+    const long long q = (nch + maxco - 1) / maxco;
+    const long long grid = std::min<long long>(4096, std::max<long long>(1, (nch + q - 1) / q));
+    if (q > MAX_CPC) return fail(MD_E_LIMIT, "more than %d chunks per CTA: raise per_thread", MAX_CPC);
+    MD_CUDA_TRY(cudaMemcpyAsync(s->d_chunks, ch.data(), sizeof(int4) * ch.size(),
+                                cudaMemcpyHostToDevice, s->st));
+    s->smem = smem;
+    s->grid = (int)grid;
     s->block = block;
+    s->ppt = ppt;
+    s->sd.chunks = s->d_chunks;
+    s->sd.nchunks = (int)nch;
+    s->sd.ppt = ppt;
     return MD_OK;
 }
 
@@ -258,6 +459,8 @@ int status_to_code(int ds) {
     if (ds & DS_TIMEOUT) return fail(MD_E_TIMEOUT, "device barrier wait timed out");
     if (ds & DS_NONFINITE) return fail(MD_E_NONFINITE, "non-finite position encountered");
     if (ds & DS_SKIN) return fail(MD_E_SKIN, "a particle moved more than one cell in one step");
+    if (ds & DS_NBR_OVERFLOW)
+        return fail(MD_E_LIMIT, "neighbour list overflow: raise md_params.nbr_max");
     return MD_OK;
 }
 
@@ -361,6 +564,10 @@ int observe(md_system *s, ObsArgs a) {
     return MD_OK;
 }
 
+// Particles per thread in a chunk: one, i.e. chunks of one block, which
+// keeps the staging buffers small and deals the most chunks round-robin.
+int default_ppt(const md_system *) { return 1; }
+
 long long windows_done(const md_system *s, int k) {
     const long long t = s->step - s->n_equil;
     if (t < 0) return 0;
@@ -412,8 +619,8 @@ int md_init_batch(const md_params *p, int32_t n_rep, const double *x, const doub
         const double sc2 = q.sigma * q.sigma / (q.rc * q.rc), sc6 = sc2 * sc2 * sc2;
         R.vshift = 4.0 * q.eps * (sc6 * sc6 - sc6);
         R.mass = q.mass;
-        R.trig_lo = -0.45 * q.skin;
-        R.trig_hi = h + 0.45 * q.skin;
+        R.rv2 = (q.rc + q.skin) * (q.rc + q.skin);
+        R.half_skin = 0.5 * q.skin;
         for (int d = 0; d < s->n_dx; ++d) {
             R.lx[d] = q.lx[d];
             R.dxl[d] = R.L / (double)q.lx[d];
@@ -424,8 +631,7 @@ int md_init_batch(const md_params *p, int32_t n_rep, const double *x, const doub
         R.rc2f = (float)R.rc2;
         R.epsf = (float)R.eps;
         R.sig2f = (float)R.sig2;
-        R.trig_lof = (float)R.trig_lo;
-        R.trig_hif = (float)R.trig_hi;
+        R.rv2f = (float)R.rv2;
         s->reps.push_back(R);
         pbase += R.cap;
         cbase += (long long)R.nc * R.nc + 1;
@@ -435,6 +641,17 @@ int md_init_batch(const md_params *p, int32_t n_rep, const double *x, const doub
         delete s;
         return fail(MD_E_LIMIT, "md_init_batch: more than 2^31 slots or cells");
     }
+    // neighbour-list capacity: three times the mean count within rv plus
+    // eight standard deviations (clustered replicas), or the caller's value
+    double kmax = 16.0;
+    for (int r = 0; r < n_rep; ++r) {
+        const md_params &q = p[r];
+        const double rv = q.rc + q.skin;
+        const double mean = M_PI * rv * rv * (double)q.n / (s->reps[r].L * s->reps[r].L);
+        kmax = std::max(kmax, 3.0 * mean + 8.0 * std::sqrt(mean) + 8.0);
+        if (q.nbr_max > 0) kmax = std::max(kmax, (double)q.nbr_max);
+    }
+    s->K = (int)std::min(1024.0, std::ceil(kmax / 4.0) * 4.0);
     s->nslots = (int)pbase;
     s->total_cells = (int)cbase;
     s->ntot = ibase;
@@ -466,6 +683,10 @@ int md_init_batch(const md_params *p, int32_t n_rep, const double *x, const doub
     ALLOC(S.newcell, sizeof(int32_t) * ns);
     ALLOC(S.rank, sizeof(int32_t) * ns);
     ALLOC(S.perm, sizeof(int32_t) * ns);
+    ALLOC(S.nbr, sizeof(uint32_t) * ns * (size_t)s->K);
+    ALLOC(S.nn, sizeof(int32_t) * (ns + 16));   // staged four at a time
+    s->chunk_cap = (long long)(ns / 128) + n_rep + 1;
+    ALLOC(s->d_chunks, sizeof(int4) * s->chunk_cap);
     ALLOC(S.blocksum, sizeof(int32_t) * 4096);
     ALLOC(S.snap_cell, sizeof(uint32_t) * nlg * s->ntot);
     ALLOC(S.snap_off, vsz * nlg * s->ntot);
@@ -500,6 +721,7 @@ int md_init_batch(const md_params *p, int32_t n_rep, const double *x, const doub
     S.n_equil = s->n_equil;
     for (int k = 0; k < MD_MAX_LG; ++k) S.lg_every[k] = s->lg_every[k];
     S.ntot = s->ntot;
+    S.K = s->K;
     S.timeout_ns = 4000000000ull;
     auto tryc = [&](cudaError_t er) {
         if (er != cudaSuccess && rc == MD_OK) rc = fail(MD_E_CUDA, "md_init_batch: %s", cudaGetErrorString(er));
@@ -507,6 +729,7 @@ int md_init_batch(const md_params *p, int32_t n_rep, const double *x, const doub
     tryc(cudaMemcpyAsync(s->d_reps, s->reps.data(), sizeof(RepDev) * n_rep, cudaMemcpyHostToDevice, s->st));
     tryc(cudaMemcpyAsync(s->d_gran, gran.data(), sizeof(int32_t) * gran.size(), cudaMemcpyHostToDevice, s->st));
     tryc(cudaMemsetAsync(s->d_ctl, 0, sizeof(Control), s->st));
+    tryc(cudaMemsetAsync(S.perm, 0xff, sizeof(int32_t) * ns, s->st));   // padding slots: -1
     tryc(cudaMemsetAsync(S.cellcnt, 0, sizeof(int32_t) * s->total_cells, s->st));
     tryc(cudaMemsetAsync(S.hist, 0, sizeof(int32_t) * nhist, s->st));
     tryc(cudaMemsetAsync(S.ovf, 0, sizeof(unsigned long long) * n_rep * nlg * s->n_dx, s->st));
@@ -517,7 +740,7 @@ int md_init_batch(const md_params *p, int32_t n_rep, const double *x, const doub
         k_nc_of_id<<<(s->nslots + 255) / 256, 256, 0, s->st>>>(S, s->d_nc_of_id);
         tryc(cudaGetLastError());
     }
-    if (rc == MD_OK) rc = configure_launch(s, 256);
+    if (rc == MD_OK) rc = configure_launch(s, 256, default_ppt(s));
     if (rc == MD_OK) rc = upload_state(s, x, y, vx, vy);
     if (rc) {
         md_destroy(s);
@@ -547,6 +770,13 @@ int md_step(md_system *s, int64_t nsteps) {
     s->step += nsteps;
     s->phase_half = 1;
     return MD_OK;
+}
+
+int md_tune(md_system *s, int32_t block_threads, int32_t per_thread) {
+    if (!s) return fail(MD_E_ARG, "md_tune: NULL system");
+    if (block_threads == 0) block_threads = 256;
+    if (per_thread == 0) per_thread = default_ppt(s);
+    return configure_launch(s, block_threads, per_thread);
 }
 
 int md_sync(md_system *s) {
@@ -731,4 +961,39 @@ int feq_measured(md_system *s, int32_t rep, int32_t lg, int32_t dxi, int32_t sym
     return MD_OK;
 }
 
+int feq_batch(md_system *s, int32_t lg, int32_t dxi, int32_t symmetrize, double *out) {
+    if (!s || !out || lg < 0 || lg >= s->n_lg || dxi < 0 || dxi >= s->n_dx)
+        return fail(MD_E_ARG, "feq_batch: bad arguments");
+    FeqBatchArgs A{};
+    A.reps = s->d_reps;
+    A.hist = s->sd.hist;
+    A.ovf = s->sd.ovf;
+    A.mom = s->sd.mom;
+    A.n_lg = s->n_lg;
+    A.n_dx = s->n_dx;
+    A.lg = lg;
+    A.dxi = dxi;
+    A.nb = s->nb;
+    A.W = s->W;
+    A.sym = symmetrize != 0;
+    A.nwin = windows_done(s, lg);
+    const size_t bytes = sizeof(double) * (size_t)s->nrep * (3 * s->nb + FEQB_STATS);
+    cudaPointerAttributes at{};
+    const bool dev = cudaPointerGetAttributes(&at, out) == cudaSuccess && at.type == cudaMemoryTypeDevice;
+    cudaGetLastError();
+    double *dst = out;
+    if (!dev) MD_CUDA_TRY(cudaMallocAsync((void **)&dst, bytes, s->st));
+    A.out = dst;
+    k_feq_batch<<<s->nrep, FEQB_THREADS, 0, s->st>>>(A);
+    cudaError_t e = cudaGetLastError();
+    if (!dev) {
+        if (e == cudaSuccess) e = cudaMemcpyAsync(out, dst, bytes, cudaMemcpyDeviceToHost, s->st);
+        cudaFreeAsync(dst, s->st);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s->st);
+    }
+    if (e != cudaSuccess) return fail(MD_E_CUDA, "feq_batch: %s", cudaGetErrorString(e));
+    return MD_OK;
+}
+
 }  // extern "C"
+

@@ -5,15 +5,29 @@
 //   * slots: replica r owns slots [pbase_r, pbase_r + cap_r), cap_r = n_r
 //     rounded up to SLOT_PAD; slots past n_r are padding, never active.
 //   * particles are sorted by MD cell (row-major cy*nc + cx) within each
-//     replica; cell_start[cbase_r + c] is the first slot of cell c.  Each
-//     replica has one extra "padding cell" after its nc^2 cells that owns
-//     its padding slots, so a single exclusive scan over all cells yields
-//     every replica's cell_start.
+//     replica, and by particle id inside a cell; cell_start[cbase_r + c] is
+//     the first slot of cell c.  Each replica has one extra "padding cell"
+//     after its nc^2 cells that owns its padding slots, so a single exclusive
+//     scan over all cells yields every replica's cell_start.
 //   * per slot: packed cell (cx | cy << 16), offset from the cell corner
 //     (Vec2<T>, double-buffered: step s reads one buffer and writes the
 //     other), velocity (Vec2<T>), particle id.  The four arrays come in two
 //     sets; a rebuild gathers the sorted particles from one set into the
 //     other.
+//   * work is cut into chunks of ppt*BLOCK consecutive slots of one replica,
+//     dealt to CTAs round-robin for the whole launch.
+//   * Verlet neighbour lists (all particles within rv = rc + skin at the last
+//     rebuild, in cell-stencil order), ELL layout interleaved by 32-slot
+//     groups: entry k of slot i is nbr[(i/32)*K*32 + k*32 + i%32], so a warp
+//     reads one entry for all its lanes in one coalesced access.  An entry
+//     packs the neighbour's slot and its cell offset (dcx+1, dcy+1).  The
+//     lists do not depend on the launch shape.
+//   * the position window of a chunk is the contiguous (periodically
+//     wrapped) slot range holding every particle of the cells from one row
+//     below the chunk's first cell to one row above its last cell; each step
+//     it is staged in shared memory with asynchronous copies, double
+//     buffered so that the next chunk's window arrives while the current
+//     chunk is computed.
 //   * sampling snapshots are indexed by particle id: packed cell + offset.
 #pragma once
 
@@ -24,18 +38,20 @@ namespace mdlg {
 
 constexpr int SLOT_PAD = 256;   // slot padding per replica (multiple of every block size)
 constexpr int GRAN = 128;       // slots per replica-lookup granule
+constexpr int MAX_CPC = 128;    // most chunks one CTA may own
 
 template <typename T> struct V2;
 template <> struct V2<float> { using type = float2; };
 template <> struct V2<double> { using type = double2; };
 
+
 struct RepDev {
     int32_t nc, cbase, pbase, n, cap, ibase;
     int32_t lx[MD_MAX_DX];
     double h, L, dt, hk, rc2, eps, sig2, vshift, mass;
-    double trig_lo, trig_hi;       // rebuild once an offset leaves [trig_lo, trig_hi)
+    double rv2, half_skin;         // Verlet radius^2, rebuild displacement bound
     double dxl[MD_MAX_DX];
-    float hf, dtf, hkf, rc2f, epsf, sig2f, trig_lof, trig_hif;
+    float hf, dtf, hkf, rc2f, epsf, sig2f, rv2f;
 };
 
 struct Control {
@@ -44,15 +60,18 @@ struct Control {
     int set, cur;
     int pad0;
     long long n_rebuilds;
-    unsigned trig[3];
+    unsigned vmax[3];     // per-step max |v| dt / half_skin (float bits), by step mod 3
+    unsigned pad1;
+    double disp;          // bound on any displacement since the last rebuild, in half skins
 };
 
 // Everything the kernels need, passed by value.
 struct SysDev {
     const RepDev *reps;
     const int32_t *gran_rep;    // replica of each GRAN-slot granule
+    const int4 *chunks;         // {rep, first slot, end slot, 0}
     Control *ctl;
-    int32_t nslots, nrep, total_cells;
+    int32_t nslots, nrep, total_cells, nchunks, ppt, K;
     int32_t n_lg, n_dx, W, nb, block_windows;
     long long n_equil;
     int32_t lg_every[MD_MAX_LG];
@@ -63,6 +82,8 @@ struct SysDev {
     void *pos[2][2];
     // cell list and rebuild scratch
     int32_t *cellcnt, *cell_start, *newcell, *rank, *perm, *blocksum;
+    uint32_t *nbr;              // [nslots/32][K][32]
+    int32_t *nn;                // neighbours of each slot
     // sampling
     uint32_t *snap_cell;        // [n_lg][ntot] by particle id
     void *snap_off;             // [n_lg][ntot] Vec2<T>
@@ -73,16 +94,77 @@ struct SysDev {
     uint64_t timeout_ns;
 };
 
+// largest staged position window of a chunk (12 KB FP32, 24 KB FP64)
+template <typename T> struct WinParts;
+template <> struct WinParts<float> { static constexpr int value = 1536; };
+template <> struct WinParts<double> { static constexpr int value = 1536; };
+
+// neighbour-list entry: [31:30] dcy+1, [29:28] dcx+1, [27:0] slot
+constexpr uint32_t NB_INDEX = (1u << 28) - 1u;
+// list entries per particle staged in shared memory with the chunk
+constexpr int NB_STAGE = 8;
+
 template <typename T> __device__ __forceinline__ T rd(double d, float f);
 template <> __device__ __forceinline__ double rd<double>(double d, float) { return d; }
 template <> __device__ __forceinline__ float rd<float>(double, float f) { return f; }
 
-// Lennard-Jones force on the particle in slot `self` (packed cell cpk,
-// offset oi) from all particles of the 3x3 block of cells around its cell
-// (Sec. 4: V = 4 eps [(s/r)^12 - (s/r)^6] for r < rc; the force is the
-// derivative of the unshifted potential).  The separation is
-// (dcx*h + off_j - off_i) per axis: the stencil offset dcx carries the
-// periodic image, so no wrap arithmetic is needed on positions.
+// 1/r^2 of a pair: the hardware reciprocal in FP32 (relative error ~1e-7,
+// far below the force tolerance), IEEE division in FP64.
+__device__ __forceinline__ float inv_r2(float r2) { return __fdividef(1.0f, r2); }
+__device__ __forceinline__ double inv_r2(double r2) { return 1.0 / r2; }
+
+// Lennard-Jones sum (Sec. 4: V = 4 eps [(s/r)^12 - (s/r)^6] for r < rc, the
+// force being the derivative of the unshifted potential) over slots [a, e)
+// of one stencil row whose three cells start at a, m1, m2: the column
+// offset of slot j follows from which cell it falls in.  One loop per row
+// instead of one per cell keeps the lanes of a warp busier, since their
+// candidate counts vary less over a row than over single cells.  pos and
+// self refer to the same index space.  Every force evaluation of the
+// library goes through this one routine, so the step kernel and the
+// observation kernel produce identical bits.
+__device__ __forceinline__ float fmaT(float a, float b, float c) { return __fmaf_rn(a, b, c); }
+__device__ __forceinline__ double fmaT(double a, double b, double c) { return __fma_rn(a, b, c); }
+
+// One pair: separation (rx, ry) = x_j - x_i; accumulates the force on i.
+// Written with explicit fused multiply-adds so that every caller evaluates
+// it with the same roundings.
+template <typename T, bool kPE>
+__device__ __forceinline__ void lj_pair_acc(T rx, T ry, T rc2, T eps24, T sig2, T &fx, T &fy,
+                                            double vshift, double &pe, double &fabs_sum) {
+    const T r2 = fmaT(rx, rx, ry * ry);
+    if (r2 < rc2) {
+        const T ir2 = inv_r2(r2);
+        const T s2 = sig2 * ir2;
+        const T s6 = s2 * s2 * s2;
+        const T fr = eps24 * s6 * fmaT(T(2), s6, T(-1)) * ir2;
+        fx = fmaT(-fr, rx, fx);
+        fy = fmaT(-fr, ry, fy);
+        if (kPE) {
+            const double d6 = (double)s6;
+            pe += 0.5 * ((double)eps24 / 6.0 * (d6 * d6 - d6) - vshift);
+            fabs_sum += fabs((double)fr) * sqrt((double)r2);
+        }
+    }
+}
+
+template <typename T, bool kPE>
+__device__ __forceinline__ void lj_row(const typename V2<T>::type *pos, int a, int m1, int m2,
+                                       int e, int self, T sxm, T sx0, T sxp, T sy, T rc2,
+                                       T eps24, T sig2, T &fx, T &fy, double vshift, double &pe,
+                                       double &fabs_sum) {
+    for (int j = a; j < e; ++j) {
+        if (j == self) continue;
+        const typename V2<T>::type o = pos[j];
+        const T sx = j < m1 ? sxm : (j < m2 ? sx0 : sxp);
+        lj_pair_acc<T, kPE>(o.x + sx, o.y + sy, rc2, eps24, sig2, fx, fy, vshift, pe, fabs_sum);
+    }
+}
+
+// Force on the particle in slot `self` (packed cell cpk, offset oi) from all
+// particles of the 3x3 block of cells around its cell, read from global
+// memory.  The separation is (dcx*h + off_j - off_i) per axis: the stencil
+// offset dcx carries the periodic image.  Same row/cell order and the same
+// arithmetic as lj_window.
 template <typename T, bool kPE>
 __device__ __forceinline__ void lj_stencil(const RepDev &R, const typename V2<T>::type *pos,
                                            const int32_t *cs, uint32_t cpk,
@@ -92,35 +174,221 @@ __device__ __forceinline__ void lj_stencil(const RepDev &R, const typename V2<T>
     const int cx = (int)(cpk & 0xffffu), cy = (int)(cpk >> 16);
     const T h = rd<T>(R.h, R.hf);
     const T rc2 = rd<T>(R.rc2, R.rc2f);
-    const T eps = rd<T>(R.eps, R.epsf);
+    const T eps24 = T(24) * rd<T>(R.eps, R.epsf);
     const T sig2 = rd<T>(R.sig2, R.sig2f);
+    const T sxm = -h - oi.x, sx0 = -oi.x, sxp = h - oi.x;
     const int32_t *csr = cs + R.cbase;
+    const bool interior = cx >= 1 && cx <= nc - 2;
 #pragma unroll
     for (int oy = -1; oy <= 1; ++oy) {
         const int row = wrap1(cy + oy, nc) * nc;
         const T sy = (T)oy * h - oi.y;
+        if (interior) {
+            const int c0 = row + cx - 1;
+            lj_row<T, kPE>(pos, csr[c0], csr[c0 + 1], csr[c0 + 2], csr[c0 + 3], self, sxm, sx0, sxp,
+                           sy, rc2, eps24, sig2, fx, fy, R.vshift, pe, fabs_sum);
+        } else {
 #pragma unroll
+            for (int ox = -1; ox <= 1; ++ox) {
+                const int c = row + wrap1(cx + ox, nc);
+                const T sx = ox < 0 ? sxm : (ox == 0 ? sx0 : sxp);
+                const int e = csr[c + 1];
+                lj_row<T, kPE>(pos, csr[c], e, e, e, self, sx, sx, sx, sy, rc2, eps24, sig2, fx, fy,
+                               R.vshift, pe, fabs_sum);
+            }
+        }
+    }
+}
+
+// ---------------------------------------------------------------- chunk windows
+// Window of one chunk, fixed between two rebuilds: U0 = first slot in
+// "unwrapped" numbering (slot + k*n across the periodic seam), npw = window
+// particles, ok = the window fits the staging buffer.
+struct ChunkDesc {
+    int start, end, rep, U0, npw, ok, pad0, pad1;
+};
+
+__device__ __forceinline__ int unwrapped_start(const int32_t *csr, int c, int nc2, int n) {
+    if (c < 0) return csr[c + nc2] - n;
+    if (c >= nc2) return csr[c - nc2] + n;
+    return csr[c];
+}
+
+// Descriptor of chunk ch from the current cell list: cells [cf - nc - 1,
+// cl + nc + 1] (circularly), or the whole replica when that is shorter.
+__device__ __forceinline__ ChunkDesc make_desc(const SysDev &S, const uint32_t *cell, int ch,
+                                               int max_parts) {
+    const int4 cd = S.chunks[ch];
+    const RepDev &R = S.reps[cd.x];
+    const int nc2 = R.nc * R.nc;
+    const int32_t *csr = S.cell_start + R.cbase;
+    const uint32_t a = cell[cd.y], b = cell[cd.z - 1];
+    const int cf = (int)(a >> 16) * R.nc + (int)(a & 0xffffu);
+    const int cl = (int)(b >> 16) * R.nc + (int)(b & 0xffffu);
+    const int wlen = cl - cf + 2 * R.nc + 3;
+    int w0, ncw;
+    if (wlen >= nc2) {
+        w0 = 0;
+        ncw = nc2;
+    } else {
+        w0 = cf - R.nc - 1;
+        ncw = wlen;
+    }
+    ChunkDesc d;
+    d.start = cd.y;
+    d.end = cd.z;
+    d.rep = cd.x;
+    d.U0 = unwrapped_start(csr, w0, nc2, R.n);
+    d.npw = unwrapped_start(csr, w0 + ncw, nc2, R.n) - d.U0;
+    d.ok = d.npw <= max_parts;
+    d.pad0 = d.pad1 = 0;
+    return d;
+}
+
+// Position of slot j in the window of d, or -1 if outside it.
+__device__ __forceinline__ int window_index(const ChunkDesc &d, const RepDev &R, int j) {
+    int u = j - d.U0;
+    u = u < 0 ? u + R.n : (u >= R.n ? u - R.n : u);
+    return u < d.npw ? u : -1;
+}
+
+__device__ __forceinline__ unsigned smem_u32(const void *p) {
+    return (unsigned)__cvta_generic_to_shared(p);
+}
+template <typename V> __device__ __forceinline__ void cp_async_v(V *dst, const V *src);
+template <> __device__ __forceinline__ void cp_async_v<float2>(float2 *d, const float2 *s) {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(smem_u32(d)), "l"(s) : "memory");
+}
+template <> __device__ __forceinline__ void cp_async_v<double2>(double2 *d, const double2 *s) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_u32(d)), "l"(s) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N> __device__ __forceinline__ void cp_async_wait() {
+    asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
+}
+
+__device__ __forceinline__ void cp_async16(void *d, const void *s) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_u32(d)), "l"(s) : "memory");
+}
+
+// Shared-memory staging buffer of one chunk.
+template <typename T> struct Stage {
+    typename V2<T>::type *pos;   // window positions [WinParts]
+    typename V2<T>::type *vel;   // own velocities [chunk]
+    int32_t *nn;                 // own neighbour counts [chunk]
+    uint32_t *ent;               // own first NB_STAGE entries, [chunk/32][NB_STAGE][32]
+};
+
+// Issues the asynchronous copies of chunk d into one staging buffer: window
+// positions, own velocities, neighbour counts and the first NB_STAGE list
+// entries of every particle.
+template <typename T, int BLOCK>
+__device__ __forceinline__ void stage_chunk(const SysDev &S, const RepDev &R, const ChunkDesc &d,
+                                            const typename V2<T>::type *pin,
+                                            const typename V2<T>::type *vel, const Stage<T> &B) {
+    const int tid = threadIdx.x;
+    if (d.ok) {
+        for (int k = tid; k < d.npw; k += BLOCK) {
+            int u = d.U0 + k - R.pbase;
+            u = u < 0 ? u + R.n : (u >= R.n ? u - R.n : u);
+            cp_async_v(&B.pos[k], &pin[R.pbase + u]);
+        }
+    }
+    const int len = d.end - d.start;
+    for (int i = tid; i < len; i += BLOCK) cp_async_v(&B.vel[i], &vel[d.start + i]);
+    for (int i = 4 * tid; i < len; i += 4 * BLOCK) cp_async16(&B.nn[i], &S.nn[d.start + i]);
+    const int ngrp = (len + 31) >> 5;
+    const int per = NB_STAGE * 32 / 4;            // 16-byte pieces per group
+    for (int t = tid; t < ngrp * per; t += BLOCK) {
+        const int g = t / per, r = t % per;
+        const uint32_t *src = S.nbr + (long long)((d.start >> 5) + g) * S.K * 32 + r * 4;
+        cp_async16(&B.ent[g * NB_STAGE * 32 + r * 4], src);
+    }
+}
+
+// Chunks are dealt to CTAs round-robin (CTA b owns chunks b, b + G, b + 2G,
+// ..., G = gridDim.x) so that dense and sparse replicas mix in every CTA.
+__device__ __forceinline__ int own_chunks(int nchunks) {
+    return nchunks > (int)blockIdx.x ? (nchunks - (int)blockIdx.x + (int)gridDim.x - 1) / (int)gridDim.x : 0;
+}
+__device__ __forceinline__ int own_chunk(int i) { return (int)blockIdx.x + i * (int)gridDim.x; }
+
+// ---------------------------------------------------------------- neighbour lists
+// Builds the list of slot i from the 3x3 cell stencil (same row/cell order
+// as lj_stencil): every j with |x_j - x_i| < rv.  Returns the count; entries
+// beyond K are not written and the count reports the overflow.
+template <typename T>
+__device__ __forceinline__ int build_list(const SysDev &S, const RepDev &R,
+                                          const typename V2<T>::type *pos, uint32_t cpk,
+                                          typename V2<T>::type oi, int self) {
+    const int nc = R.nc;
+    const int cx = (int)(cpk & 0xffffu), cy = (int)(cpk >> 16);
+    const T h = rd<T>(R.h, R.hf);
+    const T rv2 = rd<T>(R.rv2, R.rv2f);
+    const int32_t *csr = S.cell_start + R.cbase;
+    uint32_t *out = S.nbr + (long long)(self >> 5) * S.K * 32 + (self & 31);
+    int cnt = 0;
+    for (int oy = -1; oy <= 1; ++oy) {
+        const int row = wrap1(cy + oy, nc) * nc;
+        const T sy = (T)oy * h - oi.y;
         for (int ox = -1; ox <= 1; ++ox) {
             const int c = row + wrap1(cx + ox, nc);
-            const int s = csr[c], e = csr[c + 1];
             const T sx = (T)ox * h - oi.x;
-            for (int j = s; j < e; ++j) {
+            const uint32_t tag = ((uint32_t)(ox + 1) << 28) | ((uint32_t)(oy + 1) << 30);
+            for (int j = csr[c]; j < csr[c + 1]; ++j) {
+                if (j == self) continue;
                 const typename V2<T>::type o = pos[j];
                 const T rx = o.x + sx, ry = o.y + sy;
-                const T r2 = rx * rx + ry * ry;
-                if (r2 < rc2 && j != self) {
-                    const T ir2 = T(1) / r2;
-                    const T s2 = sig2 * ir2;
-                    const T s6 = s2 * s2 * s2;
-                    const T fr = T(24) * eps * s6 * (T(2) * s6 - T(1)) * ir2;
-                    fx -= fr * rx;
-                    fy -= fr * ry;
-                    if (kPE) {
-                        pe += 0.5 * (4.0 * (double)eps * ((double)s6 * (double)s6 - (double)s6) -
-                                     R.vshift);
-                        fabs_sum += fabs((double)fr) * sqrt((double)r2);
-                    }
+                if (rx * rx + ry * ry < rv2) {
+                    if (cnt < S.K) out[cnt * 32] = (uint32_t)j | tag;
+                    ++cnt;
                 }
+            }
+        }
+    }
+    return cnt;
+}
+
+// Force on slot i from its neighbour list: the same pairs, order and
+// arithmetic as lj_stencil (pairs beyond rc contribute nothing), so both
+// paths give identical bits.  Neighbours inside the chunk's staged window
+// are read from shared memory, the others (column-wrapped neighbours of
+// edge particles, chunks without a window) from global memory.
+template <typename T>
+__device__ __forceinline__ void lj_list(const SysDev &S, const RepDev &R, const ChunkDesc &d,
+                                        const typename V2<T>::type *spos, const uint32_t *sent,
+                                        const typename V2<T>::type *pin, typename V2<T>::type oi,
+                                        int self, int cnt, T &fx, T &fy) {
+    const T h = rd<T>(R.h, R.hf);
+    const T rc2 = rd<T>(R.rc2, R.rc2f);
+    const T eps24 = T(24) * rd<T>(R.eps, R.epsf);
+    const T sig2 = rd<T>(R.sig2, R.sig2f);
+    const T sxs[3] = {-h - oi.x, -oi.x, h - oi.x};
+    const T sys[3] = {-h - oi.y, -oi.y, h - oi.y};
+    const uint32_t *lst = S.nbr + (long long)(self >> 5) * S.K * 32 + (self & 31);
+    double pe_unused = 0.0, fa_unused = 0.0;
+    constexpr int U = NB_STAGE;
+    for (int k0 = 0; k0 < cnt; k0 += U) {
+        uint32_t e[U];
+        if (k0 == 0 && sent) {
+#pragma unroll
+            for (int u = 0; u < U; ++u) e[u] = u < cnt ? sent[u * 32] : 0u;
+        } else {
+#pragma unroll
+            for (int u = 0; u < U; ++u) e[u] = k0 + u < cnt ? lst[(k0 + u) * 32] : 0u;
+        }
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            if (k0 + u < cnt) {
+                const int j = (int)(e[u] & NB_INDEX);
+                int w = j - d.U0;
+                w = w < 0 ? w + R.n : (w >= R.n ? w - R.n : w);
+                const typename V2<T>::type o = (d.ok && w < d.npw) ? spos[w] : pin[j];
+                const uint32_t ox = (e[u] >> 28) & 3u, oy = e[u] >> 30;
+                const T sx = ox == 0 ? sxs[0] : (ox == 1 ? sxs[1] : sxs[2]);
+                const T sy = oy == 0 ? sys[0] : (oy == 1 ? sys[1] : sys[2]);
+                lj_pair_acc<T, false>(o.x + sx, o.y + sy, rc2, eps24, sig2, fx, fy, 0.0, pe_unused,
+                                      fa_unused);
             }
         }
     }
@@ -129,39 +397,45 @@ __device__ __forceinline__ void lj_stencil(const RepDev &R, const typename V2<T>
 // ---------------------------------------------------------------- rebuild
 // Counting sort of all particles by their current (canonical) MD cell, then
 // particles inside one cell ordered by id, so the order -- and therefore
-// every force sum -- is reproducible.  Six grid barriers.
+// every force sum -- is reproducible and independent of the launch shape;
+// then the neighbour lists.  Six grid barriers.  Padding slots keep
+// perm = -1 (set at creation).
 template <typename T, int BLOCK>
-__device__ bool rebuild(const SysDev &S, int &set, int &cur, unsigned &gen, int cbeg, int cend) {
+__device__ bool rebuild(const SysDev &S, int &set, int &cur, unsigned &gen, int nloc,
+                        ChunkDesc *s_desc) {
     using V = typename V2<T>::type;
     Control *C = S.ctl;
+    const GridBarrier bar{&C->bar_count, &C->bar_gen, &C->status};
     const int tid = threadIdx.x;
     const V *pos = static_cast<const V *>(S.pos[set][cur]);
     const uint32_t *cell = S.cell[set];
     // R1: new cell and rank inside it
-    for (int ch = cbeg; ch < cend; ++ch) {
-        const int slot = ch * BLOCK + tid;
-        const RepDev &R = S.reps[S.gran_rep[slot / GRAN]];
-        if (slot >= R.pbase + R.n) continue;
-        const V o = pos[slot];
-        const uint32_t cpk = cell[slot];
+    for (int i = 0; i < nloc; ++i) {
+        const int4 cd = S.chunks[own_chunk(i)];
+        const RepDev &R = S.reps[cd.x];
         const T h = rd<T>(R.h, R.hf);
-        const int sx = o.x >= h ? 1 : (o.x < T(0) ? -1 : 0);
-        const int sy = o.y >= h ? 1 : (o.y < T(0) ? -1 : 0);
-        const int ncx = wrap1((int)(cpk & 0xffffu) + sx, R.nc);
-        const int ncy = wrap1((int)(cpk >> 16) + sy, R.nc);
-        const int gc = R.cbase + ncy * R.nc + ncx;
-        S.newcell[slot] = gc;
-        S.rank[slot] = atomicAdd(&S.cellcnt[gc], 1);
+        for (int slot = cd.y + tid; slot < cd.z; slot += BLOCK) {
+            const V o = pos[slot];
+            const uint32_t cpk = cell[slot];
+            const int sx = o.x >= h ? 1 : (o.x < T(0) ? -1 : 0);
+            const int sy = o.y >= h ? 1 : (o.y < T(0) ? -1 : 0);
+            const int ncx = wrap1((int)(cpk & 0xffffu) + sx, R.nc);
+            const int ncy = wrap1((int)(cpk >> 16) + sy, R.nc);
+            const int gc = R.cbase + ncy * R.nc + ncx;
+            S.newcell[slot] = gc;
+            S.rank[slot] = atomicAdd(&S.cellcnt[gc], 1);
+        }
     }
-    if (!grid_sync({&C->bar_count, &C->bar_gen, &C->status}, gen, S.timeout_ns)) return false;
+    if (!grid_sync(bar, gen, S.timeout_ns)) return false;
     // R2: per-CTA sums over a contiguous segment of cells
     const int seg = (S.total_cells + gridDim.x - 1) / gridDim.x;
     const int s0 = min(S.total_cells, (int)blockIdx.x * seg), s1 = min(S.total_cells, s0 + seg);
+    __shared__ int s_w[BLOCK / 32];
+    __shared__ int s_base;
     {
         int acc = 0;
         for (int c = s0 + tid; c < s1; c += BLOCK) acc += S.cellcnt[c];
         for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-        __shared__ int s_w[BLOCK / 32];
         if ((tid & 31) == 0) s_w[tid >> 5] = acc;
         __syncthreads();
         if (tid == 0) {
@@ -170,14 +444,13 @@ __device__ bool rebuild(const SysDev &S, int &set, int &cur, unsigned &gen, int 
             S.blocksum[blockIdx.x] = t;
         }
     }
-    if (!grid_sync({&C->bar_count, &C->bar_gen, &C->status}, gen, S.timeout_ns)) return false;
+    if (!grid_sync(bar, gen, S.timeout_ns)) return false;
     // R3: exclusive scan into cell_start
     {
-        __shared__ int s_w[BLOCK / 32];
-        __shared__ int s_base;
         int acc = 0;
         for (int b = tid; b < (int)blockIdx.x; b += BLOCK) acc += S.blocksum[b];
         for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+        __syncthreads();
         if ((tid & 31) == 0) s_w[tid >> 5] = acc;
         __syncthreads();
         if (tid == 0) {
@@ -209,18 +482,15 @@ __device__ bool rebuild(const SysDev &S, int &set, int &cur, unsigned &gen, int 
         }
         if ((int)blockIdx.x == (int)gridDim.x - 1 && tid == 0) S.cell_start[S.total_cells] = base;
     }
-    if (!grid_sync({&C->bar_count, &C->bar_gen, &C->status}, gen, S.timeout_ns)) return false;
+    if (!grid_sync(bar, gen, S.timeout_ns)) return false;
     // R4: scatter slot numbers to their new place; reset counts
-    for (int ch = cbeg; ch < cend; ++ch) {
-        const int slot = ch * BLOCK + tid;
-        const RepDev &R = S.reps[S.gran_rep[slot / GRAN]];
-        if (slot >= R.pbase + R.n)
-            S.perm[slot] = -1;    // padding slots keep their place
-        else
+    for (int i = 0; i < nloc; ++i) {
+        const int4 cd = S.chunks[own_chunk(i)];
+        for (int slot = cd.y + tid; slot < cd.z; slot += BLOCK)
             S.perm[S.cell_start[S.newcell[slot]] + S.rank[slot]] = slot;
     }
     for (int c = s0 + tid; c < s1; c += BLOCK) S.cellcnt[c] = 0;
-    if (!grid_sync({&C->bar_count, &C->bar_gen, &C->status}, gen, S.timeout_ns)) return false;
+    if (!grid_sync(bar, gen, S.timeout_ns)) return false;
     // R5: order each cell's particles by id; restore the padding-cell counts
     {
         const int32_t *pid = S.pid[set];
@@ -243,7 +513,7 @@ __device__ bool rebuild(const SysDev &S, int &set, int &cur, unsigned &gen, int 
             S.cellcnt[R.cbase + R.nc * R.nc] = R.cap - R.n;
         }
     }
-    if (!grid_sync({&C->bar_count, &C->bar_gen, &C->status}, gen, S.timeout_ns)) return false;
+    if (!grid_sync(bar, gen, S.timeout_ns)) return false;
     // R6: gather into the other set with canonical offsets
     {
         const int ns = set ^ 1;
@@ -251,30 +521,54 @@ __device__ bool rebuild(const SysDev &S, int &set, int &cur, unsigned &gen, int 
         V *nvel = static_cast<V *>(S.vel[ns]);
         const V *vel = static_cast<const V *>(S.vel[set]);
         const int32_t *pid = S.pid[set];
-        for (int ch = cbeg; ch < cend; ++ch) {
-            const int slot = ch * BLOCK + tid;
-            const RepDev &R = S.reps[S.gran_rep[slot / GRAN]];
-            if (slot >= R.pbase + R.n) continue;
-            const int old = S.perm[slot];
-            V o = pos[old];
-            const uint32_t cpk = cell[old];
+        for (int i = 0; i < nloc; ++i) {
+            const int4 cd = S.chunks[own_chunk(i)];
+            const RepDev &R = S.reps[cd.x];
             const T h = rd<T>(R.h, R.hf);
-            const int sx = o.x >= h ? 1 : (o.x < T(0) ? -1 : 0);
-            const int sy = o.y >= h ? 1 : (o.y < T(0) ? -1 : 0);
-            o.x -= (T)sx * h;
-            o.y -= (T)sy * h;
-            const int ncx = wrap1((int)(cpk & 0xffffu) + sx, R.nc);
-            const int ncy = wrap1((int)(cpk >> 16) + sy, R.nc);
-            npos[slot] = o;
-            nvel[slot] = vel[old];
-            S.pid[ns][slot] = pid[old];
-            S.cell[ns][slot] = (uint32_t)ncx | ((uint32_t)ncy << 16);
+            for (int slot = cd.y + tid; slot < cd.z; slot += BLOCK) {
+                const int old = S.perm[slot];
+                V o = pos[old];
+                const uint32_t cpk = cell[old];
+                const int sx = o.x >= h ? 1 : (o.x < T(0) ? -1 : 0);
+                const int sy = o.y >= h ? 1 : (o.y < T(0) ? -1 : 0);
+                o.x -= (T)sx * h;
+                o.y -= (T)sy * h;
+                const int ncx = wrap1((int)(cpk & 0xffffu) + sx, R.nc);
+                const int ncy = wrap1((int)(cpk >> 16) + sy, R.nc);
+                npos[slot] = o;
+                nvel[slot] = vel[old];
+                S.pid[ns][slot] = pid[old];
+                S.cell[ns][slot] = (uint32_t)ncx | ((uint32_t)ncy << 16);
+            }
         }
     }
-    if (!grid_sync({&C->bar_count, &C->bar_gen, &C->status}, gen, S.timeout_ns)) return false;
+    if (!grid_sync(bar, gen, S.timeout_ns)) return false;
     set ^= 1;
     cur = 0;
-    if (blockIdx.x == 0 && tid == 0) C->n_rebuilds += 1;
+    // R7: chunk windows and neighbour lists of the CTA's own slots (read only
+    // by this CTA, so no barrier follows)
+    {
+        const V *npos = static_cast<const V *>(S.pos[set][0]);
+        const uint32_t *ncell = S.cell[set];
+        for (int i = tid; i < nloc; i += BLOCK)
+            s_desc[i] = make_desc(S, ncell, own_chunk(i), WinParts<T>::value);
+        __syncthreads();
+        int over = 0;
+        for (int i = 0; i < nloc; ++i) {
+            const ChunkDesc d = s_desc[i];
+            const RepDev &R = S.reps[d.rep];
+            for (int slot = d.start + tid; slot < d.end; slot += BLOCK) {
+                const int cnt = build_list<T>(S, R, npos, ncell[slot], npos[slot], slot);
+                S.nn[slot] = cnt < S.K ? cnt : S.K;
+                over |= cnt > S.K;
+            }
+        }
+        if (__syncthreads_or(over) && tid == 0) atomicOr(&C->status, (int)DS_NBR_OVERFLOW);
+    }
+    if (blockIdx.x == 0 && tid == 0) {
+        C->n_rebuilds += 1;
+        C->disp = 0.0;
+    }
     return true;
 }
 
@@ -299,36 +593,130 @@ __device__ __forceinline__ void flush_hist(const SysDev &S, int *sh, int rep, un
     }
 }
 
-// ---------------------------------------------------------------- persistent step kernel
-// Advances all replicas by nsteps velocity-Verlet steps.  Per step and slot:
-// force F_s at the current offsets; v += (dt/2m) F twice (the first kick
-// completes the previous step unless velocities are at an integer step);
-// off += dt v into the other position buffer; on sampling steps the new
-// position is binned against the particle's snapshot (Eq. n_i) and becomes
-// the new snapshot.  One grid barrier per step; a cell-list rebuild follows
-// any step after which a particle strayed 0.45 skin outside its cell.
-template <typename T, int BLOCK>
-__global__ void __launch_bounds__(BLOCK) k_md_persistent(SysDev S, long long step0, long long nsteps,
-                                                         int phase_half, int force_rebuild) {
+// MDLG sampling of one particle for interval k (Eq. n_i): lattice cells of
+// its snapshot and its current position on every lattice, the displacement
+// class of each, the continuous displacement moments; the current position
+// becomes the snapshot.  bins[d] = -1 when nothing is to be counted.
+template <typename T>
+__device__ __forceinline__ void sample_particle(const SysDev &S, const RepDev &R, int rep, int k,
+                                                bool bin, int id, uint32_t cpk,
+                                                typename V2<T>::type on, int *bins, double &m2,
+                                                double &m4) {
     using V = typename V2<T>::type;
-    extern __shared__ int sh_hist[];
+    uint32_t *scell = S.snap_cell + (long long)k * S.ntot;
+    V *soff = static_cast<V *>(S.snap_off) + (long long)k * S.ntot;
+    const int cx = (int)(cpk & 0xffffu), cy = (int)(cpk >> 16);
+    if (bin) {
+        const uint32_t spk = scell[id];
+        const V so = soff[id];
+        const int scx = (int)(spk & 0xffffu), scy = (int)(spk >> 16);
+        int dcx = cx - scx, dcy = cy - scy;
+        const int half = R.nc / 2;
+        if (dcx > half) dcx -= R.nc; else if (dcx < -half) dcx += R.nc;
+        if (dcy > half) dcy -= R.nc; else if (dcy < -half) dcy += R.nc;
+        const double ex = (double)dcx * R.h + ((double)on.x - (double)so.x);
+        const double ey = (double)dcy * R.h + ((double)on.y - (double)so.y);
+        const double ex2 = ex * ex, ey2 = ey * ey;
+        m2 = ex2 + ey2;
+        m4 = ex2 * ex2 + ey2 * ey2;
+        const double x1 = cell_position(cx, R.h, (double)on.x);
+        const double y1 = cell_position(cy, R.h, (double)on.y);
+        const double x0 = cell_position(scx, R.h, (double)so.x);
+        const double y0 = cell_position(scy, R.h, (double)so.y);
+        for (int d = 0; d < S.n_dx; ++d) {
+            const int lx = R.lx[d];
+            const double dxl = R.dxl[d];
+            const long long ddx = lattice_shift(lattice_cell(x1, dxl, lx) - lattice_cell(x0, dxl, lx), lx);
+            const long long ddy = lattice_shift(lattice_cell(y1, dxl, lx) - lattice_cell(y0, dxl, lx), lx);
+            if (ddx >= -S.W && ddx <= S.W && ddy >= -S.W && ddy <= S.W)
+                bins[d] = (int)((ddy + S.W) * (2 * S.W + 1) + (ddx + S.W));
+            else
+                atomicAdd(&S.ovf[((long long)rep * S.n_lg + k) * S.n_dx + d], 1ull);
+        }
+    }
+    scell[id] = cpk;
+    soff[id] = on;
+}
+
+// Dynamic shared memory of the persistent kernel: sampling histograms,
+// chunk descriptors, two staging buffers (window positions, own velocities).
+__host__ __device__ inline size_t align16(size_t x) { return (x + 15) / 16 * 16; }
+__host__ __device__ inline size_t smem_hist_bytes(int n_lg, int n_dx, int nb) {
+    return align16((size_t)n_lg * n_dx * nb * sizeof(int));
+}
+template <typename T>
+__host__ __device__ inline size_t stage_bytes(int chunk) {
+    using V = typename V2<T>::type;
+    return align16((size_t)WinParts<T>::value * sizeof(V)) + align16((size_t)chunk * sizeof(V)) +
+           align16((size_t)(chunk + 4) * sizeof(int32_t)) +
+           align16((size_t)chunk * NB_STAGE * sizeof(uint32_t));
+}
+template <typename T>
+__device__ inline Stage<T> stage_at(unsigned char *p, int chunk) {
+    using V = typename V2<T>::type;
+    Stage<T> B;
+    B.pos = reinterpret_cast<V *>(p);
+    p += align16((size_t)WinParts<T>::value * sizeof(V));
+    B.vel = reinterpret_cast<V *>(p);
+    p += align16((size_t)chunk * sizeof(V));
+    B.nn = reinterpret_cast<int32_t *>(p);
+    p += align16((size_t)(chunk + 4) * sizeof(int32_t));
+    B.ent = reinterpret_cast<uint32_t *>(p);
+    return B;
+}
+template <typename T>
+__host__ __device__ inline size_t smem_bytes(int n_lg, int n_dx, int nb, int chunk) {
+    return smem_hist_bytes(n_lg, n_dx, nb) + align16(MAX_CPC * sizeof(ChunkDesc)) +
+           2 * stage_bytes<T>(chunk);
+}
+
+// ---------------------------------------------------------------- persistent step kernel
+// Advances all replicas by nsteps velocity-Verlet steps (Sec. 4).  Per step:
+//   force pass -- per slot: force F_s from the neighbour list; v += (dt/2m) F
+//     twice (the first kick completes the previous step unless velocities are
+//     at an integer step); off += dt v into the other position buffer; the
+//     largest |v| dt of the step is reduced grid-wide;
+//   grid barrier;
+//   sampling pass (steps t = n_equil + m*lg_every[k] only) -- bin each new
+//     position against its snapshot (Eq. n_i) and replace the snapshot;
+//   rebuild (cell list + neighbour lists) once the accumulated bound on
+//     displacements since the last rebuild reaches half the skin: until then
+//     no pair can have come within rc without being listed.
+template <typename T, int BLOCK>
+__global__ void __launch_bounds__(BLOCK, BLOCK == 256 ? 4 : 8) k_md_persistent(SysDev S, long long step0,
+                                                                           long long nsteps,
+                                                                           int phase_half,
+                                                                           int force_rebuild) {
+    using V = typename V2<T>::type;
+    extern __shared__ __align__(16) unsigned char smem[];
+    const int chunk = S.ppt * BLOCK;
+    const size_t hb = smem_hist_bytes(S.n_lg, S.n_dx, S.nb);
+    int *sh_hist = reinterpret_cast<int *>(smem);
+    ChunkDesc *s_desc = reinterpret_cast<ChunkDesc *>(smem + hb);
+    unsigned char *stg = smem + hb + align16(MAX_CPC * sizeof(ChunkDesc));
+    const Stage<T> B0 = stage_at<T>(stg, chunk), B1 = stage_at<T>(stg + stage_bytes<T>(chunk), chunk);
     __shared__ unsigned s_due;
     __shared__ long long s_win[MD_MAX_LG];
-    __shared__ int s_trig;
+    __shared__ float s_vmax[BLOCK / 32];
     Control *C = S.ctl;
+    const GridBarrier bar{&C->bar_count, &C->bar_gen, &C->status};
     const int tid = threadIdx.x, lane = tid & 31;
     unsigned gen = 0;
     if (tid == 0) gen = ld_acquire_gpu(&C->bar_gen);
     int set = C->set, cur = C->cur;
-    const int nchunks = S.nslots / BLOCK;
-    const int q = (nchunks + gridDim.x - 1) / gridDim.x;
-    const int cbeg = min(nchunks, (int)blockIdx.x * q), cend = min(nchunks, cbeg + q);
+    double disp = C->disp;
+    const int nloc = own_chunks(S.nchunks);
     const int per_lg = S.n_dx * S.nb;
     for (int e = tid; e < S.n_lg * per_lg; e += BLOCK) sh_hist[e] = 0;
 
     if (force_rebuild) {
-        if (!rebuild<T, BLOCK>(S, set, cur, gen, cbeg, cend)) return;
+        if (!rebuild<T, BLOCK>(S, set, cur, gen, nloc, s_desc)) return;
+        disp = 0.0;
+    } else {
+        for (int i = tid; i < nloc; i += BLOCK)
+            s_desc[i] = make_desc(S, S.cell[set], own_chunk(i), WinParts<T>::value);
     }
+    __syncthreads();
     for (long long it = 0; it < nsteps; ++it) {
         const long long s = step0 + it;
         if (tid == 0) {
@@ -343,148 +731,145 @@ __global__ void __launch_bounds__(BLOCK) k_md_persistent(SysDev S, long long ste
                 }
             }
             s_due = due;
-            s_trig = 0;
-            if (blockIdx.x == 0) C->trig[(s + 1) % 3] = 0u;
+            if (blockIdx.x == 0) C->vmax[(s + 1) % 3] = 0u;
         }
-        __syncthreads();
-        const unsigned due = s_due;
         const bool first = (it == 0) ? (phase_half == 0) : false;
         const V *pin = static_cast<const V *>(S.pos[set][cur]);
         V *pout = static_cast<V *>(S.pos[set][cur ^ 1]);
         V *vel = static_cast<V *>(S.vel[set]);
-        const uint32_t *cell = S.cell[set];
-        const int32_t *pid = S.pid[set];
-        int hist_rep = -1;
-        bool trig = false;
-        for (int ch = cbeg; ch < cend; ++ch) {
-            const int slot = ch * BLOCK + tid;
-            const int rep = S.gran_rep[(ch * BLOCK) / GRAN];
-            const RepDev &R = S.reps[rep];
-            if (due && rep != hist_rep) {
-                if (hist_rep >= 0) {
-                    __syncthreads();
-                    flush_hist(S, sh_hist, hist_rep, due, s_win);
-                    __syncthreads();
-                }
-                hist_rep = rep;
-            }
-            const bool active = slot < R.pbase + R.n;
-            V on;
-            uint32_t cpk = 0;
-            int myid = 0;
-            if (active) {
-                const V oi = pin[slot];
-                cpk = cell[slot];
-                V v = vel[slot];
+        float vm = 0.0f;   // largest |v| dt / (skin/2) of this CTA's particles
+        bool bad = false;
+        // ---- force pass: chunk i+1 is staged while chunk i is computed
+        if (nloc > 0) stage_chunk<T, BLOCK>(S, S.reps[s_desc[0].rep], s_desc[0], pin, vel, B0);
+        cp_async_commit();
+        for (int i = 0; i < nloc; ++i) {
+            const bool odd = i & 1;
+            if (i + 1 < nloc)
+                stage_chunk<T, BLOCK>(S, S.reps[s_desc[i + 1].rep], s_desc[i + 1], pin, vel,
+                                      odd ? B0 : B1);
+            cp_async_commit();
+            cp_async_wait<1>();
+            __syncthreads();
+            const ChunkDesc d = s_desc[i];
+            const RepDev &R = S.reps[d.rep];
+            const Stage<T> &B = odd ? B1 : B0;
+            const T hk = rd<T>(R.hk, R.hkf), dt = rd<T>(R.dt, R.dtf);
+            const float vscale = (float)(R.dt / R.half_skin);
+            for (int li = tid; li < d.end - d.start; li += BLOCK) {
+                const int slot = d.start + li;
+                const int cnt = B.nn[li];
+                V oi;
+                const V v0 = B.vel[li];
+                V v = v0;
+                const int ks = d.ok ? window_index(d, R, slot) : -1;
+                oi = ks >= 0 ? B.pos[ks] : pin[slot];
                 T fx = T(0), fy = T(0);
-                double pe_unused = 0.0, fa_unused = 0.0;
-                lj_stencil<T, false>(R, pin, S.cell_start, cpk, oi, slot, fx, fy, pe_unused,
-                                     fa_unused);
-                const T hk = rd<T>(R.hk, R.hkf), dt = rd<T>(R.dt, R.dtf);
+                lj_list<T>(S, R, d, B.pos, B.ent + (li >> 5) * NB_STAGE * 32 + (li & 31), pin, oi,
+                           slot, cnt, fx, fy);
                 if (!first) {
                     v.x = v.x + hk * fx;
                     v.y = v.y + hk * fy;
                 }
                 v.x = v.x + hk * fx;
                 v.y = v.y + hk * fy;
+                V on;
                 on.x = oi.x + dt * v.x;
                 on.y = oi.y + dt * v.y;
                 pout[slot] = on;
                 vel[slot] = v;
-                const T lo = rd<T>(R.trig_lo, R.trig_lof), hi = rd<T>(R.trig_hi, R.trig_hif);
-                if (!(on.x >= lo && on.x < hi && on.y >= lo && on.y < hi)) {
-                    trig = true;
-                    const T h = rd<T>(R.h, R.hf);
-                    // not finite, or more than one cell beyond its own cell
-                    if (!(on.x >= -h && on.x < T(2) * h && on.y >= -h && on.y < T(2) * h))
-                        atomicOr(&C->status, isfinite((double)on.x) && isfinite((double)on.y)
-                                                 ? (int)DS_SKIN
-                                                 : (int)DS_NONFINITE);
-                }
-                if (due) myid = pid[slot];
+                const float sp = sqrtf((float)(v.x * v.x + v.y * v.y)) * vscale;
+                vm = fmaxf(vm, sp);
+                bad |= !(sp < 1e30f);   // non-finite velocity
             }
-            if (due) {
-                // MDLG sampling of this step's new positions
-                for (int k = 0; k < S.n_lg; ++k) {
-                    if (!(due >> k & 1u)) continue;
-                    double m2 = 0.0, m4 = 0.0;
-                    uint32_t *scell = S.snap_cell + (long long)k * S.ntot;
-                    V *soff = static_cast<V *>(S.snap_off) + (long long)k * S.ntot;
-                    int bins[MD_MAX_DX];
-#pragma unroll
-                    for (int d = 0; d < MD_MAX_DX; ++d) bins[d] = -1;
+            __syncthreads();   // this buffer is refilled for chunk i+2
+        }
+        cp_async_wait<0>();
+        for (int o = 16; o > 0; o >>= 1) vm = fmaxf(vm, __shfl_xor_sync(0xffffffffu, vm, o));
+        if (lane == 0) s_vmax[tid >> 5] = vm;
+        if (__syncthreads_or(bad) && tid == 0) atomicOr(&C->status, (int)DS_NONFINITE);
+        if (tid == 0) {
+            float m = 0.0f;
+            for (int w = 0; w < BLOCK / 32; ++w) m = fmaxf(m, s_vmax[w]);
+            atomicMax(&C->vmax[s % 3], __float_as_uint(m));   // non-negative floats order as uints
+        }
+        if (!grid_sync(bar, gen, S.timeout_ns)) return;
+        cur ^= 1;
+        // every CTA accumulates the same bound, in units of half the skin
+        disp += (double)__uint_as_float(*(volatile unsigned *)&C->vmax[s % 3]) * 1.0000001;
+        // ---- sampling pass
+        const unsigned due = s_due;
+        if (due) {
+            const V *pnow = static_cast<const V *>(S.pos[set][cur]);
+            const int32_t *pid = S.pid[set];
+            const uint32_t *cell = S.cell[set];
+            int hist_rep = -1;
+            for (int i = 0; i < nloc; ++i) {
+                const int4 cd = S.chunks[own_chunk(i)];
+                const RepDev &R = S.reps[cd.x];
+                if (cd.x != hist_rep) {
+                    if (hist_rep >= 0) {
+                        __syncthreads();
+                        flush_hist(S, sh_hist, hist_rep, due, s_win);
+                        __syncthreads();
+                    }
+                    hist_rep = cd.x;
+                }
+                for (int base = cd.y; base < cd.z; base += BLOCK) {
+                    const int slot = base + tid;
+                    const bool active = slot < cd.z;
+                    int id = 0;
+                    uint32_t cpk = 0;
+                    V on{};
                     if (active) {
-                        const int cx = (int)(cpk & 0xffffu), cy = (int)(cpk >> 16);
-                        if (s_win[k] >= 0) {
-                            const uint32_t spk = scell[myid];
-                            const V so = soff[myid];
-                            const int scx = (int)(spk & 0xffffu), scy = (int)(spk >> 16);
-                            int dcx = cx - scx, dcy = cy - scy;
-                            const int half = R.nc / 2;
-                            if (dcx > half) dcx -= R.nc; else if (dcx < -half) dcx += R.nc;
-                            if (dcy > half) dcy -= R.nc; else if (dcy < -half) dcy += R.nc;
-                            const double ex = (double)dcx * R.h + ((double)on.x - (double)so.x);
-                            const double ey = (double)dcy * R.h + ((double)on.y - (double)so.y);
-                            const double ex2 = ex * ex, ey2 = ey * ey;
-                            m2 = ex2 + ey2;
-                            m4 = ex2 * ex2 + ey2 * ey2;
-                            const double x1 = cell_position(cx, R.h, (double)on.x);
-                            const double y1 = cell_position(cy, R.h, (double)on.y);
-                            const double x0 = cell_position(scx, R.h, (double)so.x);
-                            const double y0 = cell_position(scy, R.h, (double)so.y);
-                            for (int d = 0; d < S.n_dx; ++d) {
-                                const int lx = R.lx[d];
-                                const double dxl = R.dxl[d];
-                                const long long ddx =
-                                    lattice_shift(lattice_cell(x1, dxl, lx) - lattice_cell(x0, dxl, lx), lx);
-                                const long long ddy =
-                                    lattice_shift(lattice_cell(y1, dxl, lx) - lattice_cell(y0, dxl, lx), lx);
-                                if (ddx >= -S.W && ddx <= S.W && ddy >= -S.W && ddy <= S.W)
-                                    bins[d] = (int)((ddy + S.W) * (2 * S.W + 1) + (ddx + S.W));
-                                else
-                                    atomicAdd(&S.ovf[((long long)rep * S.n_lg + k) * S.n_dx + d], 1ull);
+                        id = pid[slot];
+                        cpk = cell[slot];
+                        on = pnow[slot];
+                    }
+                    for (int k = 0; k < S.n_lg; ++k) {
+                        if (!(due >> k & 1u)) continue;
+                        const bool bin = s_win[k] >= 0;
+                        int bins[MD_MAX_DX] = {-1, -1, -1, -1};
+                        double m2 = 0.0, m4 = 0.0;
+                        if (active) sample_particle<T>(S, R, cd.x, k, bin, id, cpk, on, bins, m2, m4);
+                        if (bin) {
+                            for (int d = 0; d < S.n_dx; ++d)
+                                warp_hist_add(sh_hist + k * per_lg + d * S.nb, bins[d], lane);
+                            for (int o = 16; o > 0; o >>= 1) {
+                                m2 += __shfl_xor_sync(0xffffffffu, m2, o);
+                                m4 += __shfl_xor_sync(0xffffffffu, m4, o);
+                            }
+                            if (lane == 0 && (base + (tid & ~31)) < cd.z) {
+                                double *mp = S.mom + ((long long)(slot >> 5) * S.n_lg + k) * 2;
+                                mp[0] += m2;
+                                mp[1] += m4;
                             }
                         }
-                        scell[myid] = cpk;
-                        soff[myid] = on;
-                    }
-                    if (s_win[k] >= 0) {
-                        for (int d = 0; d < S.n_dx; ++d)
-                            warp_hist_add(sh_hist + k * per_lg + d * S.nb, bins[d], lane);
-                        for (int o = 16; o > 0; o >>= 1) {
-                            m2 += __shfl_xor_sync(0xffffffffu, m2, o);
-                            m4 += __shfl_xor_sync(0xffffffffu, m4, o);
-                        }
-                        if (lane == 0) {
-                            double *mp = S.mom + ((long long)(slot >> 5) * S.n_lg + k) * 2;
-                            mp[0] += m2;
-                            mp[1] += m4;
-                        }
                     }
                 }
             }
+            if (hist_rep >= 0) {
+                __syncthreads();
+                flush_hist(S, sh_hist, hist_rep, due, s_win);
+            }
         }
-        if (due && hist_rep >= 0) {
-            __syncthreads();
-            flush_hist(S, sh_hist, hist_rep, due, s_win);
+        if (disp >= 1.0) {
+            if (!rebuild<T, BLOCK>(S, set, cur, gen, nloc, s_desc)) return;
+            disp = 0.0;
         }
-        if (__syncthreads_or(trig) && tid == 0) atomicOr(&C->trig[s % 3], 1u);
-        if (!grid_sync({&C->bar_count, &C->bar_gen, &C->status}, gen, S.timeout_ns)) return;
-        cur ^= 1;
-        if (*(volatile unsigned *)&C->trig[s % 3]) {
-            if (!rebuild<T, BLOCK>(S, set, cur, gen, cbeg, cend)) return;
-        }
+        __syncthreads();   // s_due / s_win / s_vmax are rewritten in the next step
     }
     if (blockIdx.x == 0 && tid == 0) {
         C->set = set;
         C->cur = cur;
+        C->disp = disp;
     }
 }
 
 // ---------------------------------------------------------------- observation kernel
 // One pass at the current step without moving particles: forces, optional
 // completion of the half kick (velocities then refer to the current step),
-// per-warp energy/momentum partials, and outputs in particle-id order.
+// per-warp energy/momentum partials, outputs in particle-id order, and
+// snapshots for the sampling slots in snap_mask.
 struct ObsArgs {
     int complete;          // apply v += (dt/2m) F (velocities were half-step)
     double *epart;         // [nslots/32][4] KE, PE, Px, Py or NULL

@@ -38,7 +38,7 @@ class md_params(C.Structure):
         ("precision", C.c_int32), ("W", C.c_int32), ("n_equil", C.c_int64),
         ("n_lg", C.c_int32), ("lg_every", C.c_int32 * MD_MAX_LG),
         ("n_dx", C.c_int32), ("lx", C.c_int32 * MD_MAX_DX),
-        ("block_windows", C.c_int32), ("reserved", C.c_int32),
+        ("block_windows", C.c_int32), ("nbr_max", C.c_int32),
     ]
 
 
@@ -72,6 +72,7 @@ _SIGS = {
     "md_destroy": ([P], None),
     "md_step": ([P, C.c_int64], C.c_int),
     "md_sync": ([P], C.c_int),
+    "md_tune": ([P, C.c_int32, C.c_int32], C.c_int),
     "md_info": ([P, C.POINTER(md_info_t)], C.c_int),
     "md_rep_info": ([P, C.c_int32, C.POINTER(md_rep_info_t)], C.c_int),
     "md_get_state": ([P, P, P, P, P], C.c_int),
@@ -83,6 +84,7 @@ _SIGS = {
     "md_hist_raw": ([P, C.c_int32, C.c_int32, C.c_int32, P, P, P], C.c_int),
     "feq_measured": ([P, C.c_int32, C.c_int32, C.c_int32, C.c_int32, P, P,
                       C.POINTER(md_feq_stats)], C.c_int),
+    "feq_batch": ([P, C.c_int32, C.c_int32, C.c_int32, P], C.c_int),
     "mdlg_bin": ([C.POINTER(md_snapshot), C.POINTER(md_snapshot), C.c_int64, C.c_int32, C.c_int32,
                   P, P, P, P], C.c_int),
     "feq_gaussian": ([C.c_double, C.c_double, C.c_double, C.c_int32, P, P], C.c_int),
@@ -187,6 +189,9 @@ class System:
     def sync(self):
         _check(load().md_sync(self.h))
 
+    def tune(self, block_threads=0, per_thread=0):
+        _check(load().md_tune(self.h, block_threads, per_thread))
+
     def info(self):
         o = md_info_t()
         _check(load().md_info(self.h, C.byref(o)))
@@ -249,6 +254,25 @@ class System:
         _check(load().feq_measured(self.h, rep, lg, dxi, int(symmetrize), _ptr(Pm), _ptr(se),
                                    C.byref(st)))
         return Pm, se, st
+
+
+FEQB_STATS = 16
+FEQB_FIELDS = ("mu2", "mu4", "a2", "lambda", "maxabs_g", "kl_g", "maxabs_wsg", "kl_wsg",
+               "n_windows", "n_samples", "n_overflow", "dx_eff", "lambda_status", "sum_p")
+
+
+def feq_batch(system, lg=0, dxi=0, symmetrize=True, out=None):
+    """Batched f_eq stage; returns (P_md, P_g, P_wsg, stats) as arrays of shape
+    [n_rep, nb] / [n_rep, 16] (host), or fills a device tensor `out`."""
+    nrep = len(system.params)
+    nb = system.nb
+    stride = 3 * nb + FEQB_STATS
+    if out is not None:
+        _check(load().feq_batch(system.h, lg, dxi, int(symmetrize), _ptr(out)))
+        return out
+    buf = np.zeros((nrep, stride))
+    _check(load().feq_batch(system.h, lg, dxi, int(symmetrize), _ptr(buf)))
+    return buf[:, :nb], buf[:, nb:2 * nb], buf[:, 2 * nb:3 * nb], buf[:, 3 * nb:]
 
 
 def mdlg_bin(cell0, ox0, oy0, cell1, ox1, oy1, ncell, h, lx, W, stream=None):

@@ -348,3 +348,59 @@ def test_wsg_closer_than_gaussian_in_paper_regime(mdlg):
     assert acc[c] / gn[c] > 1.0          # node 0 enhanced
     assert acc[c + 1] / gn[c + 1] < 1.0  # first layer depressed
     s.close()
+
+
+def test_results_independent_of_launch_shape(mdlg):
+    """Particle order, force sums and reductions are fixed by the data, so the
+    trajectory and histograms are bit-identical for every launch shape."""
+    n = 50_000
+    st, L = _state(n, 0.0784, 20.0, seed=9)
+    p = mdlg.make_params(n, L, precision=mdlg.MD_FP32_CELLOFF, lg_every=(100, 300),
+                         lx=(int(L), int(L / 2)))
+    out = []
+    for block, ppt in ((256, 1), (128, 4), (256, 8)):
+        s = mdlg.System(p, st.x, st.y, st.vx, st.vy)
+        s.tune(block, ppt)
+        s.step(900)
+        out.append((s.get_state(), s.hist_raw(0, 1, 1), s.feq_measured(0, 0, 0)[2].mu4))
+        s.close()
+    for o in out[1:]:
+        for u, v in zip(out[0][0], o[0]):
+            assert np.array_equal(u, v)
+        assert np.array_equal(out[0][1][0], o[1][0]) and out[0][2] == o[2]
+
+
+def test_feq_batch_matches_single_calls_and_oracle(mdlg, orc):
+    """The one-launch f_eq stage equals feq_measured per replica and the
+    oracle's Gaussian / WSG / lambda / KL at the measured moments."""
+    R = 6
+    Ns, phis, Ts = inputs.ensemble_params(R, seed=3, n_min=2000, n_max=8000)
+    params, cat = [], [[], [], [], []]
+    for r in range(R):
+        L = inputs.box_length(int(Ns[r]), float(phis[r]))
+        st = inputs.lattice_gas_state(int(Ns[r]), L, float(Ts[r]), seed=40 + r)
+        params.append(mdlg.make_params(int(Ns[r]), L, precision=mdlg.MD_FP32_CELLOFF, W=4,
+                                       lg_every=(200, 600), lx=(int(round(L / 1.5)),)))
+        for a, f in zip(cat, ("x", "y", "vx", "vy")):
+            a.append(getattr(st, f))
+    s = mdlg.System(params, *[np.concatenate(a) for a in cat])
+    s.step(3000)
+    for lg in (0, 1):
+        Pm, G, Wg, stt = mdlg.feq_batch(s, lg, 0, symmetrize=True)
+        for r in range(R):
+            P1, _, st1 = s.feq_measured(r, lg, 0, symmetrize=True)
+            assert np.array_equal(Pm[r], P1)
+            assert stt[r, 0] == st1.mu2 and stt[r, 1] == st1.mu4
+            a2 = stt[r, 2]
+            assert np.max(np.abs(G[r] - orc.feq_gaussian(a2, 0, 0, 4))) < 1e-12
+            rc, l1, l2 = orc.wsg_lambda(st1.mu2, st1.mu4)
+            lam = stt[r, 3]
+            if rc == 0 and 3.0 < st1.mu4 / st1.mu2 ** 2 <= 3.75 and l2 <= 1e5:
+                assert abs(lam - l2) < 1e-9 * max(1.0, l2)
+            else:
+                assert stt[r, 12] != 0
+            assert np.max(np.abs(Wg[r] - orc.feq_wsg(a2, lam, 0, 0, 4))) < 1e-12
+            assert abs(stt[r, 5] - orc.kl(Pm[r], G[r])) < 1e-12
+            assert abs(stt[r, 7] - orc.kl(Pm[r], Wg[r])) < 1e-12
+            assert abs(stt[r, 4] - np.max(np.abs(Pm[r] - G[r]))) < 1e-15
+    s.close()
