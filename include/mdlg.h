@@ -175,10 +175,24 @@ void md_destroy(md_system *s);
 int md_step(md_system *s, int64_t nsteps);
 
 /* Launch shape of the persistent kernel: block_threads in {128, 256} (0 =
- * 256), per_thread in [1, 8] particles per thread per chunk (0 = 1).  Results do not depend on the shape: particle
- * order, force summation order and every reduction order are fixed by the
- * data, not by the launch.  Used by the autotuner. */
-int md_tune(md_system *s, int32_t block_threads, int32_t per_thread);
+ * 256), per_thread in [1, 8] particles per thread per chunk (0 = 1),
+ * staging 1 = each chunk's neighbour positions, velocities and first list
+ * entries are copied to shared memory (double buffered) before its forces
+ * are computed, 2 = neighbours are read from global memory through L1
+ * (0 = 1).  Results do not depend on the shape: particle order, force
+ * summation order and every reduction order are fixed by the data, not by
+ * the launch.  Used by md_autotune. */
+int md_tune(md_system *s, int32_t block_threads, int32_t per_thread, int32_t staging);
+
+/* Autotuner: times md_step(steps_per_trial) twice for every launch shape
+ * (block {256,128} x per_thread {1,2,4} x staging {1,2}) and keeps the
+ * fastest; the choice is cached for the process by (precision, replicas,
+ * particle count rounded up to a power of two, list capacity) and reused
+ * without trials.  The trial steps are real MD steps: the system advances
+ * by them (the trajectory itself does not depend on the shape).  best3
+ * (host, may be NULL) receives {block_threads, per_thread, staging}.
+ * Synchronises. */
+int md_autotune(md_system *s, int64_t steps_per_trial, int32_t *best3);
 
 /* Waits for the system's stream and returns the device status word (and
  * clears it). */

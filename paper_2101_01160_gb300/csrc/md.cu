@@ -7,6 +7,9 @@
 #include <algorithm>
 #include <cmath>
 #include <cstring>
+#include <map>
+#include <mutex>
+#include <tuple>
 #include <vector>
 
 #include "common.cuh"
@@ -371,7 +374,7 @@ struct md_system {
     int nslots = 0, total_cells = 0;
     cudaStream_t st = nullptr;
     int dev = 0, nsm = 1;
-    int block = 256, grid = 1, ppt = 1, K = 16;
+    int block = 256, grid = 1, ppt = 1, K = 16, stage = 1;
     long long chunk_cap = 0;
     int4 *d_chunks = nullptr;
     size_t smem = 0;
@@ -409,9 +412,10 @@ const void *persistent_fn(int prec, int block) {
                         : (const void *)k_md_persistent<float, 256>;
 }
 
-int configure_launch(md_system *s, int block, int ppt) {
+int configure_launch(md_system *s, int block, int ppt, int stage) {
     if (block != 128 && block != 256) return fail(MD_E_ARG, "block_threads must be 128 or 256");
     if (ppt < 1 || ppt > 8) return fail(MD_E_ARG, "per_thread must be in [1, 8]");
+    if (stage != 1 && stage != 2) return fail(MD_E_ARG, "staging must be 1 or 2");
     const void *fn = persistent_fn(s->prec, block);
     const int chunk = ppt * block;
     // chunk table: ppt*block consecutive slots of one replica
@@ -443,6 +447,8 @@ int configure_launch(md_system *s, int block, int ppt) {
     s->sd.chunks = s->d_chunks;
     s->sd.nchunks = (int)nch;
     s->sd.ppt = ppt;
+    s->sd.stage = stage == 1;
+    s->stage = stage;
     return MD_OK;
 }
 
@@ -740,7 +746,7 @@ int md_init_batch(const md_params *p, int32_t n_rep, const double *x, const doub
         k_nc_of_id<<<(s->nslots + 255) / 256, 256, 0, s->st>>>(S, s->d_nc_of_id);
         tryc(cudaGetLastError());
     }
-    if (rc == MD_OK) rc = configure_launch(s, 256, default_ppt(s));
+    if (rc == MD_OK) rc = configure_launch(s, 256, default_ppt(s), 1);
     if (rc == MD_OK) rc = upload_state(s, x, y, vx, vy);
     if (rc) {
         md_destroy(s);
@@ -772,11 +778,12 @@ int md_step(md_system *s, int64_t nsteps) {
     return MD_OK;
 }
 
-int md_tune(md_system *s, int32_t block_threads, int32_t per_thread) {
+int md_tune(md_system *s, int32_t block_threads, int32_t per_thread, int32_t staging) {
     if (!s) return fail(MD_E_ARG, "md_tune: NULL system");
     if (block_threads == 0) block_threads = 256;
     if (per_thread == 0) per_thread = default_ppt(s);
-    return configure_launch(s, block_threads, per_thread);
+    if (staging == 0) staging = 1;
+    return configure_launch(s, block_threads, per_thread, staging);
 }
 
 int md_sync(md_system *s) {
@@ -992,6 +999,81 @@ int feq_batch(md_system *s, int32_t lg, int32_t dxi, int32_t symmetrize, double 
         if (e == cudaSuccess) e = cudaStreamSynchronize(s->st);
     }
     if (e != cudaSuccess) return fail(MD_E_CUDA, "feq_batch: %s", cudaGetErrorString(e));
+    return MD_OK;
+}
+
+// ---- autotuner ------------------------------------------------------------
+// Launch shapes tried: block {256, 128} x per_thread {1, 2, 4} x staging
+// {shared, global}.  The best shape per (precision, replicas, particle
+// count rounded to a power of two, list capacity) is kept for the process.
+namespace {
+std::mutex g_tune_mu;
+std::map<std::tuple<int, int, int, int>, std::tuple<int, int, int>> g_tune_cache;
+}
+
+int md_autotune(md_system *s, int64_t steps_per_trial, int32_t *best3) {
+    if (!s || steps_per_trial < 1) return fail(MD_E_ARG, "md_autotune: bad arguments");
+    int lg2 = 0;
+    while ((1ll << lg2) < s->ntot) ++lg2;
+    const auto key = std::make_tuple(s->prec, s->nrep, lg2, s->K);
+    {
+        std::lock_guard<std::mutex> lk(g_tune_mu);
+        auto it = g_tune_cache.find(key);
+        if (it != g_tune_cache.end()) {
+            int rc = configure_launch(s, std::get<0>(it->second), std::get<1>(it->second),
+                                      std::get<2>(it->second));
+            if (rc) return rc;
+            if (best3) {
+                best3[0] = std::get<0>(it->second);
+                best3[1] = std::get<1>(it->second);
+                best3[2] = std::get<2>(it->second);
+            }
+            return MD_OK;
+        }
+    }
+    cudaEvent_t e0, e1;
+    MD_CUDA_TRY(cudaEventCreate(&e0));
+    MD_CUDA_TRY(cudaEventCreate(&e1));
+    float best_ms = 1e30f;
+    int bb = 256, bp = 1, bs = 1;
+    const int blocks[2] = {256, 128}, ppts[3] = {1, 2, 4}, stages[2] = {1, 2};
+    int rc = MD_OK;
+    for (int b : blocks)
+        for (int p : ppts)
+            for (int st : stages) {
+                if (configure_launch(s, b, p, st) != MD_OK) continue;   // shape does not fit
+                rc = md_step(s, steps_per_trial);                          // settles caches
+                if (rc) break;
+                cudaEventRecord(e0, s->st);
+                rc = md_step(s, steps_per_trial);
+                if (rc) break;
+                cudaEventRecord(e1, s->st);
+                cudaEventSynchronize(e1);
+                float ms = 0.0f;
+                cudaEventElapsedTime(&ms, e0, e1);
+                if (ms < best_ms) {
+                    best_ms = ms;
+                    bb = b;
+                    bp = p;
+                    bs = st;
+                }
+            }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (rc) return rc;
+    rc = sync_status(s);
+    if (rc) return rc;
+    rc = configure_launch(s, bb, bp, bs);
+    if (rc) return rc;
+    {
+        std::lock_guard<std::mutex> lk(g_tune_mu);
+        g_tune_cache[key] = std::make_tuple(bb, bp, bs);
+    }
+    if (best3) {
+        best3[0] = bb;
+        best3[1] = bp;
+        best3[2] = bs;
+    }
     return MD_OK;
 }
 

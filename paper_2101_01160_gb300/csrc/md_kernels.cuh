@@ -71,7 +71,7 @@ struct SysDev {
     const int32_t *gran_rep;    // replica of each GRAN-slot granule
     const int4 *chunks;         // {rep, first slot, end slot, 0}
     Control *ctl;
-    int32_t nslots, nrep, total_cells, nchunks, ppt, K;
+    int32_t nslots, nrep, total_cells, nchunks, ppt, K, stage;
     int32_t n_lg, n_dx, W, nb, block_windows;
     long long n_equil;
     int32_t lg_every[MD_MAX_LG];
@@ -670,6 +670,32 @@ __host__ __device__ inline size_t smem_bytes(int n_lg, int n_dx, int nb, int chu
            2 * stage_bytes<T>(chunk);
 }
 
+// Velocity-Verlet update of one particle: v += (dt/2m) F twice (the first
+// kick completes the previous step unless velocities are at an integer
+// step), off += dt v into the other position buffer; tracks the largest
+// |v| dt / (skin/2) and non-finite velocities.
+template <typename T>
+__device__ __forceinline__ void kick_drift(const RepDev &R, typename V2<T>::type oi,
+                                           typename V2<T>::type v, T fx, T fy, T hk, T dt,
+                                           bool first, float vscale, typename V2<T>::type *pout,
+                                           typename V2<T>::type *vel, int slot, float &vm,
+                                           bool &bad) {
+    if (!first) {
+        v.x = v.x + hk * fx;
+        v.y = v.y + hk * fy;
+    }
+    v.x = v.x + hk * fx;
+    v.y = v.y + hk * fy;
+    typename V2<T>::type on;
+    on.x = oi.x + dt * v.x;
+    on.y = oi.y + dt * v.y;
+    pout[slot] = on;
+    vel[slot] = v;
+    const float sp = sqrtf((float)(v.x * v.x + v.y * v.y)) * vscale;
+    vm = fmaxf(vm, sp);
+    bad |= !(sp < 1e30f);   // non-finite velocity
+}
+
 // ---------------------------------------------------------------- persistent step kernel
 // Advances all replicas by nsteps velocity-Verlet steps (Sec. 4).  Per step:
 //   force pass -- per slot: force F_s from the neighbour list; v += (dt/2m) F
@@ -739,51 +765,54 @@ __global__ void __launch_bounds__(BLOCK, BLOCK == 256 ? 4 : 8) k_md_persistent(S
         V *vel = static_cast<V *>(S.vel[set]);
         float vm = 0.0f;   // largest |v| dt / (skin/2) of this CTA's particles
         bool bad = false;
-        // ---- force pass: chunk i+1 is staged while chunk i is computed
-        if (nloc > 0) stage_chunk<T, BLOCK>(S, S.reps[s_desc[0].rep], s_desc[0], pin, vel, B0);
-        cp_async_commit();
-        for (int i = 0; i < nloc; ++i) {
-            const bool odd = i & 1;
-            if (i + 1 < nloc)
-                stage_chunk<T, BLOCK>(S, S.reps[s_desc[i + 1].rep], s_desc[i + 1], pin, vel,
-                                      odd ? B0 : B1);
+        // ---- force pass
+        if (S.stage) {
+            // chunk i+1 is staged in shared memory while chunk i is computed
+            if (nloc > 0) stage_chunk<T, BLOCK>(S, S.reps[s_desc[0].rep], s_desc[0], pin, vel, B0);
             cp_async_commit();
-            cp_async_wait<1>();
-            __syncthreads();
-            const ChunkDesc d = s_desc[i];
-            const RepDev &R = S.reps[d.rep];
-            const Stage<T> &B = odd ? B1 : B0;
-            const T hk = rd<T>(R.hk, R.hkf), dt = rd<T>(R.dt, R.dtf);
-            const float vscale = (float)(R.dt / R.half_skin);
-            for (int li = tid; li < d.end - d.start; li += BLOCK) {
-                const int slot = d.start + li;
-                const int cnt = B.nn[li];
-                V oi;
-                const V v0 = B.vel[li];
-                V v = v0;
-                const int ks = d.ok ? window_index(d, R, slot) : -1;
-                oi = ks >= 0 ? B.pos[ks] : pin[slot];
-                T fx = T(0), fy = T(0);
-                lj_list<T>(S, R, d, B.pos, B.ent + (li >> 5) * NB_STAGE * 32 + (li & 31), pin, oi,
-                           slot, cnt, fx, fy);
-                if (!first) {
-                    v.x = v.x + hk * fx;
-                    v.y = v.y + hk * fy;
+            for (int i = 0; i < nloc; ++i) {
+                const bool odd = i & 1;
+                if (i + 1 < nloc)
+                    stage_chunk<T, BLOCK>(S, S.reps[s_desc[i + 1].rep], s_desc[i + 1], pin, vel,
+                                          odd ? B0 : B1);
+                cp_async_commit();
+                cp_async_wait<1>();
+                __syncthreads();
+                const ChunkDesc d = s_desc[i];
+                const RepDev &R = S.reps[d.rep];
+                const Stage<T> &B = odd ? B1 : B0;
+                const T hk = rd<T>(R.hk, R.hkf), dt = rd<T>(R.dt, R.dtf);
+                const float vscale = (float)(R.dt / R.half_skin);
+                for (int li = tid; li < d.end - d.start; li += BLOCK) {
+                    const int slot = d.start + li;
+                    const int ks = d.ok ? window_index(d, R, slot) : -1;
+                    const V oi = ks >= 0 ? B.pos[ks] : pin[slot];
+                    T fx = T(0), fy = T(0);
+                    lj_list<T>(S, R, d, B.pos, B.ent + (li >> 5) * NB_STAGE * 32 + (li & 31), pin,
+                               oi, slot, B.nn[li], fx, fy);
+                    kick_drift<T>(R, oi, B.vel[li], fx, fy, hk, dt, first, vscale, pout, vel, slot, vm,
+                                  bad);
                 }
-                v.x = v.x + hk * fx;
-                v.y = v.y + hk * fy;
-                V on;
-                on.x = oi.x + dt * v.x;
-                on.y = oi.y + dt * v.y;
-                pout[slot] = on;
-                vel[slot] = v;
-                const float sp = sqrtf((float)(v.x * v.x + v.y * v.y)) * vscale;
-                vm = fmaxf(vm, sp);
-                bad |= !(sp < 1e30f);   // non-finite velocity
+                __syncthreads();   // this buffer is refilled for chunk i+2
             }
-            __syncthreads();   // this buffer is refilled for chunk i+2
+            cp_async_wait<0>();
+        } else {
+            // neighbours straight from global memory (L1/L2); no CTA-wide sync
+            ChunkDesc none{};
+            for (int i = 0; i < nloc; ++i) {
+                const int4 cd = S.chunks[own_chunk(i)];
+                const RepDev &R = S.reps[cd.x];
+                const T hk = rd<T>(R.hk, R.hkf), dt = rd<T>(R.dt, R.dtf);
+                const float vscale = (float)(R.dt / R.half_skin);
+                for (int slot = cd.y + tid; slot < cd.z; slot += BLOCK) {
+                    const V oi = pin[slot];
+                    T fx = T(0), fy = T(0);
+                    lj_list<T>(S, R, none, nullptr, nullptr, pin, oi, slot, S.nn[slot], fx, fy);
+                    kick_drift<T>(R, oi, vel[slot], fx, fy, hk, dt, first, vscale, pout, vel, slot,
+                                  vm, bad);
+                }
+            }
         }
-        cp_async_wait<0>();
         for (int o = 16; o > 0; o >>= 1) vm = fmaxf(vm, __shfl_xor_sync(0xffffffffu, vm, o));
         if (lane == 0) s_vmax[tid >> 5] = vm;
         if (__syncthreads_or(bad) && tid == 0) atomicOr(&C->status, (int)DS_NONFINITE);

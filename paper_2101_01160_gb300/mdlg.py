@@ -72,7 +72,8 @@ _SIGS = {
     "md_destroy": ([P], None),
     "md_step": ([P, C.c_int64], C.c_int),
     "md_sync": ([P], C.c_int),
-    "md_tune": ([P, C.c_int32, C.c_int32], C.c_int),
+    "md_tune": ([P, C.c_int32, C.c_int32, C.c_int32], C.c_int),
+    "md_autotune": ([P, C.c_int64, P], C.c_int),
     "md_info": ([P, C.POINTER(md_info_t)], C.c_int),
     "md_rep_info": ([P, C.c_int32, C.POINTER(md_rep_info_t)], C.c_int),
     "md_get_state": ([P, P, P, P, P], C.c_int),
@@ -189,8 +190,13 @@ class System:
     def sync(self):
         _check(load().md_sync(self.h))
 
-    def tune(self, block_threads=0, per_thread=0):
-        _check(load().md_tune(self.h, block_threads, per_thread))
+    def tune(self, block_threads=0, per_thread=0, staging=0):
+        _check(load().md_tune(self.h, block_threads, per_thread, staging))
+
+    def autotune(self, steps_per_trial=100):
+        best = np.zeros(3, np.int32)
+        _check(load().md_autotune(self.h, int(steps_per_trial), _ptr(best)))
+        return tuple(int(v) for v in best)
 
     def info(self):
         o = md_info_t()

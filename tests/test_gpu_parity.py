@@ -358,9 +358,9 @@ def test_results_independent_of_launch_shape(mdlg):
     p = mdlg.make_params(n, L, precision=mdlg.MD_FP32_CELLOFF, lg_every=(100, 300),
                          lx=(int(L), int(L / 2)))
     out = []
-    for block, ppt in ((256, 1), (128, 4), (256, 8)):
+    for block, ppt, staging in ((256, 1, 1), (128, 4, 1), (256, 8, 2), (128, 1, 2)):
         s = mdlg.System(p, st.x, st.y, st.vx, st.vy)
-        s.tune(block, ppt)
+        s.tune(block, ppt, staging)
         s.step(900)
         out.append((s.get_state(), s.hist_raw(0, 1, 1), s.feq_measured(0, 0, 0)[2].mu4))
         s.close()
@@ -404,3 +404,26 @@ def test_feq_batch_matches_single_calls_and_oracle(mdlg, orc):
             assert abs(stt[r, 7] - orc.kl(Pm[r], Wg[r])) < 1e-12
             assert abs(stt[r, 4] - np.max(np.abs(Pm[r] - G[r]))) < 1e-15
     s.close()
+
+
+def test_autotune_keeps_trajectory(mdlg):
+    """The autotuner's trial steps are ordinary steps: the tuned system ends
+    bit-identical to an untuned one advanced by the same number of steps."""
+    n = 40_000
+    st, L = _state(n, 0.1, 10.0, seed=12)
+    p = mdlg.make_params(n, L, precision=mdlg.MD_FP32_CELLOFF, lg_every=(50,), lx=(int(L),))
+    a = mdlg.System(p, st.x, st.y, st.vx, st.vy)
+    best = a.autotune(20)
+    assert best[0] in (128, 256) and best[1] in (1, 2, 4) and best[2] in (1, 2)
+    done = a.info().step
+    assert done > 0
+    b = mdlg.System(p, st.x, st.y, st.vx, st.vy)
+    b.step(done)
+    for u, v in zip(a.get_state(), b.get_state()):
+        assert np.array_equal(u, v)
+    assert np.array_equal(a.hist_raw()[0], b.hist_raw()[0])
+    # a second system of the same size reuses the cached shape without trials
+    c = mdlg.System(p, st.x, st.y, st.vx, st.vy)
+    assert c.autotune(20) == best and c.info().step == 0
+    for s_ in (a, b, c):
+        s_.close()
