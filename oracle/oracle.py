@@ -240,7 +240,36 @@ def md_run(x, y, vx, vy, L, dt, nsteps, n_equil=0, every=(), lx=(), W=4, rc=2.5,
 
 # ---------------------------------------------------------------- MLP (surrogate)
 def _declare_mlp(L):
-    L.or_mlp_forward.argtypes = [I32, P, I64, P, P, P]
+    L.or_mlp_forward.argtypes = [I32, P, I64, P, P, P, P, P]
     L.or_mlp_forward.restype = C.c_int
     L.or_mlp_loss_backward.argtypes = [I32, P, I64, P, P, P, P, P, P]
     L.or_mlp_loss_backward.restype = D
+
+
+def mlp_pack(Ws, bs):
+    """Packs [W_1, b_1, W_2, b_2, ...] (W row-major [out][in]) into one FP64 vector."""
+    return np.concatenate([np.concatenate([np.asarray(W, np.float64).ravel(),
+                                           np.asarray(b, np.float64).ravel()])
+                           for W, b in zip(Ws, bs)])
+
+
+def mlp_forward(sizes, X, params, shift, scale):
+    sizes = np.ascontiguousarray(sizes, dtype=np.int32)
+    X = _f64(X)
+    M = X.shape[0]
+    out = np.zeros((M, int(sizes[-1])))
+    rc = lib().or_mlp_forward(len(sizes) - 1, _p(sizes), M, _p(X), _p(_f64(shift)), _p(_f64(scale)),
+                              _p(_f64(params)), _p(out))
+    assert rc == 0
+    return out
+
+
+def mlp_loss_backward(sizes, X, params, T, shift, scale):
+    sizes = np.ascontiguousarray(sizes, dtype=np.int32)
+    X = _f64(X)
+    params = _f64(params)
+    grad = np.zeros_like(params)
+    loss = lib().or_mlp_loss_backward(len(sizes) - 1, _p(sizes), X.shape[0], _p(X),
+                                      _p(_f64(shift)), _p(_f64(scale)), _p(params), _p(_f64(T)),
+                                      _p(grad))
+    return loss, grad
