@@ -301,6 +301,51 @@ int feq_wsg(double a2, double lambda, double ux, double uy, int32_t W, double *P
  * 0 log 0 = 0, sum_i R_i}.  R, Q: device. */
 int feq_compare(const double *R, const double *Q, int32_t n, double *out3, void *stream);
 
+/* ---- f_eq surrogate (a project addition, not in the paper) -------------- */
+
+/* A multilayer perceptron from the state point x = (phi, T, Delta t_LG,
+ * Delta x) to the probabilities of n_classes displacement classes: features
+ * (x - shift)/scale, n_hidden layers of width 256 with the SiLU activation
+ * (the first on CUDA cores, the others as BF16 tensor-core GEMMs with FP32
+ * accumulation), a softmax output; trained on the mean Kullback-Leibler
+ * divergence (Eq. kullback_leibler) to measured distributions with Adam.
+ * Weights are FP32 masters with BF16 copies for the tensor cores.  params
+ * (host or device, FP32) packs W_1, b_1, W_2, b_2, ... with W_l row-major
+ * [out][in]; mlp_param_count gives its length.  Device memory is owned by
+ * the model (workspace grows with the largest batch seen). */
+typedef struct mlp_model mlp_model;
+int mlp_create(int32_t n_hidden, int32_t width, int32_t n_classes, const float *shift4,
+               const float *scale4, const float *params, mlp_model **out);
+void mlp_destroy(mlp_model *m);
+int64_t mlp_param_count(mlp_model *m);
+int mlp_set_params(mlp_model *m, const float *params);
+int mlp_get_params(mlp_model *m, float *params);
+
+/* P_out[M][n_classes] = model(X[M][4]); X, P_out device FP32.  Asynchronous. */
+int mlp_forward(mlp_model *m, const float *X, int64_t M, float *P_out, void *stream);
+
+/* Gradient of the mean KL loss over a batch (X [B][4], targets T
+ * [B][n_classes], device, B a multiple of 128) into grad_out (device or host,
+ * packed like params; may be NULL) and the loss into *loss_out (device, may
+ * be NULL).  Asynchronous. */
+int mlp_grad(mlp_model *m, const float *X, const float *T, int32_t B, float *grad_out,
+             float *loss_out, void *stream);
+
+/* One Adam step (beta1 0.9, beta2 0.999, eps 1e-8) at learning rate lr on a
+ * batch.  Asynchronous. */
+int mlp_train_step(mlp_model *m, const float *X, const float *T, int32_t B, float lr,
+                   float *loss_out, void *stream);
+
+/* Waits for the device and reports a timed-out tensor-core wait
+ * (MD_E_TIMEOUT). */
+int mlp_status(mlp_model *m);
+
+/* C[M][N] (FP32) = A[M][K] * B[N][K]^T on the tensor cores; A, B BF16
+ * row-major device; M % 128 == 0, K % 64 == 0, N % 16 == 0 with N <= 256.
+ * *status (device int) gets bit 0 set if a wait timed out.  Asynchronous. */
+int bf16_gemm_tn(const void *A, const void *B, float *C, int32_t M, int32_t N, int32_t K,
+                 int32_t *status, void *stream);
+
 /* Message of the calling thread's last failure ("" if none). */
 const char *md_last_error(void);
 

@@ -1,0 +1,693 @@
+// The f_eq surrogate (a project addition, not in the paper): an MLP mapping
+// the state point (phi, T, Delta t_LG, Delta x) to the probabilities of the
+// (2W+1)^2 = 81 displacement classes, trained on histograms measured by the
+// MD of this library.  Hidden layers are BF16 GEMMs on the tensor cores
+// (tcgen05.mma, FP32 accumulation in TMEM, fused bias/activation epilogues);
+// the 4-input first layer, softmax, loss, transposes, bias gradients and
+// Adam are CUDA-core kernels.
+//
+// Model: x_f = (x - shift)/scale; h_1 = silu(W_1 x_f + b_1) (CUDA cores);
+// h_l = silu(W_l h_{l-1} + b_l), l = 2..L-1 (tensor cores); logits =
+// W_L h_{L-1} + b_L (tensor cores, classes padded to 128 with zero rows);
+// p = softmax(logits[0..81)); loss = mean D_KL(t || p).
+#include <cuda_bf16.h>
+
+#include <cmath>
+#include <cstring>
+#include <vector>
+
+#include "common.cuh"
+#include "umma.cuh"
+
+namespace mdlg {
+
+using bf16 = __nv_bfloat16;
+
+constexpr int GBM = 128;   // GEMM tile rows (TMEM lanes)
+constexpr int GBK = 64;    // K per pipeline stage
+constexpr uint64_t GEMM_WAIT_NS = 2000000000ull;
+
+enum Epi { EPI_F32 = 0, EPI_BIAS_F32 = 1, EPI_BIAS_SILU = 2, EPI_DSILU = 3 };
+
+struct GemmArgs {
+    const bf16 *A;      // [M][K] row-major (K contiguous)
+    const bf16 *B;      // [N][K] row-major
+    int lda, ldb, M, N, K;
+    float *C;           // FP32 output (EPI_F32 / EPI_BIAS_F32; pre-activation for EPI_BIAS_SILU)
+    int ldc;
+    bf16 *H;            // BF16 output (activation or gradient)
+    int ldh;
+    const float *bias;  // [N]
+    const float *Zp;    // EPI_DSILU: pre-activation, [M][ldz]
+    int ldz;
+    int *status;
+};
+
+__device__ __forceinline__ float silu(float z) { return z / (1.0f + __expf(-z)); }
+__device__ __forceinline__ float silu_grad(float z) {
+    const float s = 1.0f / (1.0f + __expf(-z));
+    return s * (1.0f + z * (1.0f - s));
+}
+
+__device__ __forceinline__ void cpa16(void *dst, const void *src) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(umma::saddr(dst)), "l"(src) : "memory");
+}
+
+// Byte offset of element (row r, k) of a K-major tile of GBK columns in the
+// no-swizzle core-matrix layout: 8x8 blocks of 128 bytes, blocks along K
+// adjacent (LBO = 128 B), 8-row groups GBK/8 blocks apart (SBO = 1024 B).
+__device__ __forceinline__ int tile_off(int r, int k8) { return (r >> 3) * 1024 + k8 * 128 + (r & 7) * 16; }
+
+// C = A * B^T on the tensor cores; one CTA computes a 128 x N tile (N <= 256,
+// a multiple of 16) with the accumulator in N TMEM columns.  K is consumed
+// in stages of 64: the loads of stage k+1 overlap the MMAs of stage k.
+template <int EPI>
+__global__ void __launch_bounds__(128) k_gemm(GemmArgs g) {
+    extern __shared__ __align__(1024) unsigned char sm[];
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int N = g.N;
+    const int a_bytes = GBM * GBK * 2, b_bytes = N * GBK * 2;
+    unsigned char *st0 = sm, *st1 = sm + a_bytes + b_bytes;
+    uint64_t *mbar = reinterpret_cast<uint64_t *>(sm + 2 * (a_bytes + b_bytes));
+    uint32_t *s_tmem = reinterpret_cast<uint32_t *>(mbar + 2);
+    __shared__ int s_ok;
+    const uint32_t ncols = N <= 32 ? 32u : (N <= 64 ? 64u : (N <= 128 ? 128u : 256u));
+    if (warp == 0) umma::tmem_alloc(s_tmem, ncols);
+    if (tid == 0) {
+        umma::mbar_init(&mbar[0], 1);
+        umma::mbar_init(&mbar[1], 1);
+        umma::mbar_fence_init();
+        s_ok = 1;
+    }
+    umma::fence_before();
+    __syncthreads();
+    umma::fence_after();
+    const uint32_t tmem = *s_tmem;
+    const int m0 = blockIdx.x * GBM;
+    const int nk = g.K / GBK;
+    const uint32_t idesc = umma::idesc_bf16(GBM, N);
+    for (int kt = 0; kt < nk; ++kt) {
+        const int s = kt & 1;
+        unsigned char *sa = s ? st1 : st0;
+        unsigned char *sb = sa + a_bytes;
+        if (kt >= 2 && !umma::mbar_wait(&mbar[s], ((kt - 2) >> 1) & 1, GEMM_WAIT_NS)) s_ok = 0;
+        __syncthreads();
+        if (!s_ok) break;
+        for (int c = tid; c < GBM * 8; c += 128) {
+            const int r = c >> 3, k8 = c & 7;
+            cpa16(sa + tile_off(r, k8), g.A + (size_t)(m0 + r) * g.lda + kt * GBK + k8 * 8);
+        }
+        for (int c = tid; c < N * 8; c += 128) {
+            const int r = c >> 3, k8 = c & 7;
+            cpa16(sb + tile_off(r, k8), g.B + (size_t)r * g.ldb + kt * GBK + k8 * 8);
+        }
+        asm volatile("cp.async.commit_group;" ::: "memory");
+        asm volatile("cp.async.wait_group 0;" ::: "memory");
+        umma::fence_proxy_smem();
+        __syncthreads();
+        if (tid == 0) {
+            umma::fence_after();
+            const uint32_t a0 = umma::saddr(sa), b0 = umma::saddr(sb);
+#pragma unroll
+            for (int k4 = 0; k4 < GBK / 16; ++k4)
+                umma::mma(tmem, umma::desc(a0 + k4 * 256, 128, 1024), umma::desc(b0 + k4 * 256, 128, 1024),
+                          idesc, (kt | k4) ? 1u : 0u);
+            umma::commit(&mbar[s]);
+        }
+    }
+    if (s_ok) {
+        const int last = nk - 1;
+        if (!umma::mbar_wait(&mbar[last & 1], (last >> 1) & 1, GEMM_WAIT_NS)) s_ok = 0;
+    }
+    __syncthreads();
+    umma::fence_after();
+    if (s_ok) {
+        const int row = m0 + warp * 32 + lane;
+        for (int c0 = 0; c0 < N; c0 += 16) {
+            float v[16];
+            umma::ld16(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0, v);
+            if (EPI == EPI_F32 || EPI == EPI_BIAS_F32) {
+                float4 *dst = reinterpret_cast<float4 *>(g.C + (size_t)row * g.ldc + c0);
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    float4 o;
+                    o.x = v[4 * q + 0] + (EPI == EPI_BIAS_F32 ? g.bias[c0 + 4 * q + 0] : 0.0f);
+                    o.y = v[4 * q + 1] + (EPI == EPI_BIAS_F32 ? g.bias[c0 + 4 * q + 1] : 0.0f);
+                    o.z = v[4 * q + 2] + (EPI == EPI_BIAS_F32 ? g.bias[c0 + 4 * q + 2] : 0.0f);
+                    o.w = v[4 * q + 3] + (EPI == EPI_BIAS_F32 ? g.bias[c0 + 4 * q + 3] : 0.0f);
+                    dst[q] = o;
+                }
+            } else {
+                __align__(16) bf16 hb[16];
+#pragma unroll
+                for (int i = 0; i < 16; ++i) {
+                    float o;
+                    if (EPI == EPI_BIAS_SILU) {
+                        const float z = v[i] + g.bias[c0 + i];
+                        if (g.C) g.C[(size_t)row * g.ldc + c0 + i] = z;
+                        o = silu(z);
+                    } else {
+                        o = v[i] * silu_grad(g.Zp[(size_t)row * g.ldz + c0 + i]);
+                    }
+                    hb[i] = __float2bfloat16_rn(o);
+                }
+                uint4 *dst = reinterpret_cast<uint4 *>(g.H + (size_t)row * g.ldh + c0);
+                dst[0] = reinterpret_cast<const uint4 *>(hb)[0];
+                dst[1] = reinterpret_cast<const uint4 *>(hb)[1];
+            }
+        }
+    } else if (tid == 0) {
+        atomicOr(g.status, 1);
+    }
+    umma::fence_before();
+    __syncthreads();
+    if (warp == 0) umma::tmem_free(tmem, ncols);
+}
+
+size_t gemm_smem(int N) { return 2 * (size_t)(GBM * GBK * 2 + N * GBK * 2) + 32; }
+
+template <int EPI>
+int gemm_launch(const GemmArgs &g, cudaStream_t st) {
+    if (g.M % GBM || g.K % GBK || g.N % 16 || g.N < 16 || g.N > 256 || g.lda % 8 || g.ldb % 8)
+        return fail(MD_E_ARG, "gemm: M %% 128, K %% 64, N %% 16 in [16,256], lda/ldb %% 8 required");
+    const size_t smem = gemm_smem(g.N);
+    MD_CUDA_TRY(cudaFuncSetAttribute(k_gemm<EPI>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    k_gemm<EPI><<<g.M / GBM, 128, smem, st>>>(g);
+    MD_CUDA_TRY(cudaGetLastError());
+    return MD_OK;
+}
+
+// ---------------------------------------------------------------- CUDA-core kernels
+// First layer (4 inputs): features, pre-activation (optional) and BF16
+// activation; rows >= M (padding) get zero features.
+__global__ void k_layer1(const float *X, int M, int Mpad, const float *W, const float *b,
+                         const float4 shift, const float4 scale, int width, float *xf, float *Z,
+                         bf16 *H) {
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= (long long)Mpad * width) return;
+    const int m = (int)(i / width), o = (int)(i % width);
+    float f0 = 0.f, f1 = 0.f, f2 = 0.f, f3 = 0.f;
+    if (m < M) {
+        f0 = (X[4 * m + 0] - shift.x) / scale.x;
+        f1 = (X[4 * m + 1] - shift.y) / scale.y;
+        f2 = (X[4 * m + 2] - shift.z) / scale.z;
+        f3 = (X[4 * m + 3] - shift.w) / scale.w;
+    }
+    if (xf && o == 0) {
+        xf[4 * m + 0] = f0;
+        xf[4 * m + 1] = f1;
+        xf[4 * m + 2] = f2;
+        xf[4 * m + 3] = f3;
+    }
+    const float z = b[o] + W[4 * o + 0] * f0 + W[4 * o + 1] * f1 + W[4 * o + 2] * f2 + W[4 * o + 3] * f3;
+    if (Z) Z[i] = z;
+    H[i] = __float2bfloat16_rn(silu(z));
+}
+
+// Softmax over the first ncls logits of each row; with targets, also the
+// row's share of the mean KL loss and d loss / d logits = (p sum(t) - t) / Mb
+// as BF16 (zero in the padding columns).
+__global__ void k_softmax(const float *logits, int ldl, int M, int ncls, float *P, const float *T,
+                          float *rowloss, bf16 *dlog, int ldd, float inv_batch) {
+    const int m = blockIdx.x * (blockDim.x / 32) + (threadIdx.x >> 5);
+    const int lane = threadIdx.x & 31;
+    if (m >= M) return;
+    const float *l = logits + (size_t)m * ldl;
+    float mx = -INFINITY;
+    for (int c = lane; c < ncls; c += 32) mx = fmaxf(mx, l[c]);
+    for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    float s = 0.f;
+    for (int c = lane; c < ncls; c += 32) s += __expf(l[c] - mx);
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    const float inv = 1.0f / s;
+    float ts = 0.f, loss = 0.f;
+    if (T)
+        for (int c = lane; c < ncls; c += 32) ts += T[(size_t)m * ncls + c];
+    for (int o = 16; o > 0; o >>= 1) ts += __shfl_xor_sync(0xffffffffu, ts, o);
+    for (int c = lane; c < ldd || c < ncls; c += 32) {
+        if (c < ncls) {
+            const float p = __expf(l[c] - mx) * inv;
+            if (P) P[(size_t)m * ncls + c] = p;
+            if (T) {
+                const float t = T[(size_t)m * ncls + c];
+                if (t > 0.f) loss += t * (__logf(t) - __logf(p));
+                if (dlog) dlog[(size_t)m * ldd + c] = __float2bfloat16_rn((p * ts - t) * inv_batch);
+            }
+        } else if (dlog && c < ldd) {
+            dlog[(size_t)m * ldd + c] = __float2bfloat16_rn(0.f);
+        }
+    }
+    if (rowloss) {
+        for (int o = 16; o > 0; o >>= 1) loss += __shfl_xor_sync(0xffffffffu, loss, o);
+        if (lane == 0) rowloss[m] = loss * inv_batch;
+    }
+}
+
+// BF16 transpose [R][C] -> [C][R] through a 32x33 shared tile.
+__global__ void k_transpose(const bf16 *in, int R, int C, bf16 *out) {
+    __shared__ bf16 t[32][33];
+    const int c0 = blockIdx.x * 32, r0 = blockIdx.y * 32;
+    for (int y = threadIdx.y; y < 32; y += blockDim.y) {
+        const int r = r0 + y, c = c0 + threadIdx.x;
+        t[y][threadIdx.x] = (r < R && c < C) ? in[(size_t)r * C + c] : __float2bfloat16_rn(0.f);
+    }
+    __syncthreads();
+    for (int y = threadIdx.y; y < 32; y += blockDim.y) {
+        const int c = c0 + y, r = r0 + threadIdx.x;
+        if (c < C && r < R) out[(size_t)c * R + r] = t[threadIdx.x][y];
+    }
+}
+
+// Column sums of a BF16 [M][N] matrix in FP32 (fixed order), into out[n].
+__global__ void k_colsum(const bf16 *a, int M, int N, int ld, float *out) {
+    const int n = blockIdx.x * blockDim.x + threadIdx.x;
+    if (n >= N) return;
+    float s = 0.f;
+    for (int m = 0; m < M; ++m) s += __bfloat162float(a[(size_t)m * ld + n]);
+    out[n] = s;
+}
+
+// dW_1 = dZ_1^T x_f (4 inputs), fixed summation order over the batch.
+__global__ void k_grad_layer1(const bf16 *dZ, int M, int width, const float *xf, float *gW) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= width * 4) return;
+    const int o = i / 4, k = i % 4;
+    float s = 0.f;
+    for (int m = 0; m < M; ++m) s += __bfloat162float(dZ[(size_t)m * width + o]) * xf[4 * m + k];
+    gW[i] = s;
+}
+
+// Adam on FP32 master parameters; refreshes the BF16 copy (and its
+// transpose) used by the tensor cores.  rows x cols block of a parameter with
+// leading dimension ld; master/m/v/g share that layout.
+__global__ void k_adam(float *w, float *mom, float *var, const float *g, int rows, int cols, int ld,
+                       float lr, float b1, float b2, float c1, float c2, float eps, bf16 *wb,
+                       bf16 *wt, int ldt) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= rows * cols) return;
+    const int r = i / cols, c = i % cols;
+    const size_t k = (size_t)r * ld + c;
+    const float gr = g[k];
+    const float m = b1 * mom[k] + (1.f - b1) * gr;
+    const float v = b2 * var[k] + (1.f - b2) * gr * gr;
+    mom[k] = m;
+    var[k] = v;
+    const float nw = w[k] - lr * (m / c1) / (sqrtf(v / c2) + eps);
+    w[k] = nw;
+    if (wb) wb[k] = __float2bfloat16_rn(nw);
+    if (wt) wt[(size_t)c * ldt + r] = __float2bfloat16_rn(nw);
+}
+
+__global__ void k_to_bf16(const float *w, int n, bf16 *out) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) out[i] = __float2bfloat16_rn(w[i]);
+}
+
+__global__ void k_sum(const float *a, int n, float *out) {
+    __shared__ float s[256];
+    float acc = 0.f;
+    for (int i = threadIdx.x; i < n; i += 256) acc += a[i];
+    s[threadIdx.x] = acc;
+    __syncthreads();
+    for (int o = 128; o > 0; o >>= 1) {
+        if ((int)threadIdx.x < o) s[threadIdx.x] += s[threadIdx.x + o];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) *out = s[0];
+}
+
+}  // namespace mdlg
+
+using namespace mdlg;
+
+// ---------------------------------------------------------------- model
+struct mlp_model {
+    int nl = 0;                   // linear layers (hidden + 1)
+    int width = 256, ncls = 81, npad = 128, nin = 4;
+    float shift[4], scale[4];
+    std::vector<int> out, in, outp;   // per layer l = 0..nl-1 (out padded in outp)
+    // FP32 master, Adam moments, gradients: per layer W [outp][in], b [outp]
+    std::vector<float *> W, b, mW, vW, mb, vb, gW, gb;
+    std::vector<bf16 *> Wh, Wt;   // BF16 [outp][in] and [in][outp] (layers >= 1)
+    int adam_t = 0;
+    // workspace
+    long long cap = 0;            // rows
+    float *xf = nullptr, *logits = nullptr, *rowloss = nullptr;
+    std::vector<float *> Z;       // [cap][width] per hidden layer
+    std::vector<bf16 *> H;        // [cap][width] per hidden layer
+    bf16 *dA = nullptr, *dB = nullptr, *dlog = nullptr, *tA = nullptr, *tB = nullptr;
+    int *status = nullptr;
+    std::vector<void *> allocs, ws;
+};
+
+namespace {
+
+int malloc_into(std::vector<void *> &v, void **p, size_t bytes) {
+    cudaError_t e = cudaMalloc(p, bytes ? bytes : 16);
+    if (e != cudaSuccess) return fail(MD_E_NOMEM, "cudaMalloc(%zu): %s", bytes, cudaGetErrorString(e));
+    v.push_back(*p);
+    return MD_OK;
+}
+
+// Grows the row workspace to hold `rows` rows (multiple of 128).
+int ensure_ws(mlp_model *m, long long rows) {
+    if (rows <= m->cap) return MD_OK;
+    cudaDeviceSynchronize();
+    for (void *p : m->ws) cudaFree(p);
+    m->ws.clear();
+    const size_t R = (size_t)rows, Wd = (size_t)m->width;
+    int rc = MD_OK;
+    auto A = [&](void **p, size_t bytes) {
+        if (rc == MD_OK) rc = malloc_into(m->ws, p, bytes);
+    };
+    A((void **)&m->xf, R * 4 * sizeof(float));
+    A((void **)&m->logits, R * m->npad * sizeof(float));
+    A((void **)&m->rowloss, R * sizeof(float));
+    m->Z.assign(m->nl - 1, nullptr);
+    m->H.assign(m->nl - 1, nullptr);
+    for (int l = 0; l < m->nl - 1; ++l) {
+        A((void **)&m->Z[l], R * Wd * sizeof(float));
+        A((void **)&m->H[l], R * Wd * sizeof(bf16));
+    }
+    A((void **)&m->dA, R * Wd * sizeof(bf16));
+    A((void **)&m->dB, R * Wd * sizeof(bf16));
+    A((void **)&m->dlog, R * m->npad * sizeof(bf16));
+    A((void **)&m->tA, R * Wd * sizeof(bf16));
+    A((void **)&m->tB, R * Wd * sizeof(bf16));
+    if (rc) return rc;
+    m->cap = rows;
+    return MD_OK;
+}
+
+int refresh_bf16(mlp_model *m, cudaStream_t st) {
+    for (int l = 1; l < m->nl; ++l) {
+        const int n = m->outp[l] * m->in[l];
+        k_to_bf16<<<(n + 255) / 256, 256, 0, st>>>(m->W[l], n, m->Wh[l]);
+        dim3 tb(32, 8), gr((m->in[l] + 31) / 32, (m->outp[l] + 31) / 32);
+        k_transpose<<<gr, tb, 0, st>>>(m->Wh[l], m->outp[l], m->in[l], m->Wt[l]);
+    }
+    MD_CUDA_TRY(cudaGetLastError());
+    return MD_OK;
+}
+
+// Forward pass on rows [0, Mpad): H_l (and Z_l when keep_z), logits.
+int forward(mlp_model *m, const float *X, long long M, long long Mpad, bool keep_z, cudaStream_t st) {
+    const float4 sh = make_float4(m->shift[0], m->shift[1], m->shift[2], m->shift[3]);
+    const float4 sc = make_float4(m->scale[0], m->scale[1], m->scale[2], m->scale[3]);
+    const long long n1 = Mpad * m->width;
+    k_layer1<<<(unsigned)((n1 + 255) / 256), 256, 0, st>>>(X, (int)M, (int)Mpad, m->W[0], m->b[0], sh,
+                                                          sc, m->width, m->xf,
+                                                          keep_z ? m->Z[0] : nullptr, m->H[0]);
+    MD_CUDA_TRY(cudaGetLastError());
+    for (int l = 1; l < m->nl; ++l) {
+        GemmArgs g{};
+        g.A = m->H[l - 1];
+        g.lda = m->width;
+        g.B = m->Wh[l];
+        g.ldb = m->in[l];
+        g.M = (int)Mpad;
+        g.N = m->outp[l];
+        g.K = m->in[l];
+        g.bias = m->b[l];
+        g.status = m->status;
+        int rc;
+        if (l < m->nl - 1) {
+            g.C = keep_z ? m->Z[l] : nullptr;
+            g.ldc = m->width;
+            g.H = m->H[l];
+            g.ldh = m->width;
+            rc = gemm_launch<EPI_BIAS_SILU>(g, st);
+        } else {
+            g.C = m->logits;
+            g.ldc = m->npad;
+            rc = gemm_launch<EPI_BIAS_F32>(g, st);
+        }
+        if (rc) return rc;
+    }
+    return MD_OK;
+}
+
+int transpose(const bf16 *in, int R, int C, bf16 *out, cudaStream_t st) {
+    dim3 tb(32, 8), gr((C + 31) / 32, (R + 31) / 32);
+    k_transpose<<<gr, tb, 0, st>>>(in, R, C, out);
+    MD_CUDA_TRY(cudaGetLastError());
+    return MD_OK;
+}
+
+// Loss (device scalar, optional) and gradients of a batch of Mb rows
+// (Mb % 128 == 0) into gW / gb.
+int backward(mlp_model *m, const float *X, const float *T, int Mb, float *loss_dev, cudaStream_t st) {
+    int rc = forward(m, X, Mb, Mb, true, st);
+    if (rc) return rc;
+    k_softmax<<<(Mb + 7) / 8, 256, 0, st>>>(m->logits, m->npad, Mb, m->ncls, nullptr, T, m->rowloss,
+                                            m->dlog, m->npad, 1.0f / (float)Mb);
+    MD_CUDA_TRY(cudaGetLastError());
+    if (loss_dev) {
+        k_sum<<<1, 256, 0, st>>>(m->rowloss, Mb, loss_dev);
+        MD_CUDA_TRY(cudaGetLastError());
+    }
+    // dZ of the current layer (layer L: dlogits) and its width
+    const bf16 *dZ = m->dlog;
+    int dzw = m->npad;
+    bf16 *bufs[2] = {m->dA, m->dB};
+    for (int l = m->nl - 1; l >= 1; --l) {
+        // dW_l = dZ^T H_{l-1}; db_l = colsum(dZ)
+        if ((rc = transpose(dZ, Mb, dzw, m->tA, st))) return rc;
+        if ((rc = transpose(m->H[l - 1], Mb, m->width, m->tB, st))) return rc;
+        GemmArgs g{};
+        g.A = m->tA;
+        g.lda = Mb;
+        g.B = m->tB;
+        g.ldb = Mb;
+        g.M = dzw;
+        g.N = m->width;
+        g.K = Mb;
+        g.C = m->gW[l];
+        g.ldc = m->in[l];
+        g.status = m->status;
+        if ((rc = gemm_launch<EPI_F32>(g, st))) return rc;
+        k_colsum<<<(dzw + 127) / 128, 128, 0, st>>>(dZ, Mb, dzw, dzw, m->gb[l]);
+        MD_CUDA_TRY(cudaGetLastError());
+        // dZ_{l-1} = (dZ W_l) * silu'(Z_{l-1})
+        GemmArgs d{};
+        d.A = dZ;
+        d.lda = dzw;
+        d.B = m->Wt[l];
+        d.ldb = m->outp[l];
+        d.M = Mb;
+        d.N = m->width;
+        d.K = dzw;
+        d.H = bufs[l & 1];
+        d.ldh = m->width;
+        d.Zp = m->Z[l - 1];
+        d.ldz = m->width;
+        d.status = m->status;
+        if ((rc = gemm_launch<EPI_DSILU>(d, st))) return rc;
+        dZ = bufs[l & 1];
+        dzw = m->width;
+    }
+    k_grad_layer1<<<(m->width * 4 + 127) / 128, 128, 0, st>>>(dZ, Mb, m->width, m->xf, m->gW[0]);
+    k_colsum<<<(m->width + 127) / 128, 128, 0, st>>>(dZ, Mb, m->width, m->width, m->gb[0]);
+    MD_CUDA_TRY(cudaGetLastError());
+    return MD_OK;
+}
+
+long long pad128(long long M) { return (M + 127) / 128 * 128; }
+
+}  // namespace
+
+extern "C" {
+
+int mlp_create(int32_t n_hidden, int32_t width, int32_t n_classes, const float *shift4,
+               const float *scale4, const float *params, mlp_model **out) {
+    if (!out || !shift4 || !scale4 || !params || n_hidden < 2 || n_hidden > 15 || width != 256 ||
+        n_classes < 2 || n_classes > 128)
+        return fail(MD_E_ARG, "mlp_create: n_hidden in [2,15], width 256, classes in [2,128]");
+    mlp_model *m = new mlp_model();
+    m->nl = n_hidden + 1;
+    m->width = width;
+    m->ncls = n_classes;
+    m->npad = 128;
+    std::memcpy(m->shift, shift4, sizeof(m->shift));
+    std::memcpy(m->scale, scale4, sizeof(m->scale));
+    for (int l = 0; l < m->nl; ++l) {
+        m->in.push_back(l == 0 ? 4 : width);
+        m->out.push_back(l == m->nl - 1 ? n_classes : width);
+        m->outp.push_back(l == m->nl - 1 ? m->npad : width);
+    }
+    int rc = MD_OK;
+    auto A = [&](void **p, size_t bytes) {
+        if (rc == MD_OK) rc = malloc_into(m->allocs, p, bytes);
+    };
+    m->W.assign(m->nl, nullptr);
+    m->b = m->mW = m->vW = m->mb = m->vb = m->gW = m->gb = m->W;
+    m->Wh.assign(m->nl, nullptr);
+    m->Wt.assign(m->nl, nullptr);
+    for (int l = 0; l < m->nl; ++l) {
+        const size_t nw = (size_t)m->outp[l] * m->in[l], nbias = (size_t)m->outp[l];
+        A((void **)&m->W[l], nw * 4);
+        A((void **)&m->mW[l], nw * 4);
+        A((void **)&m->vW[l], nw * 4);
+        A((void **)&m->gW[l], nw * 4);
+        A((void **)&m->b[l], nbias * 4);
+        A((void **)&m->mb[l], nbias * 4);
+        A((void **)&m->vb[l], nbias * 4);
+        A((void **)&m->gb[l], nbias * 4);
+        if (l > 0) {
+            A((void **)&m->Wh[l], nw * 2);
+            A((void **)&m->Wt[l], nw * 2);
+        }
+    }
+    A((void **)&m->status, sizeof(int));
+    if (rc) {
+        mlp_destroy(m);
+        return rc;
+    }
+    for (int l = 0; l < m->nl; ++l) {
+        const size_t nw = (size_t)m->outp[l] * m->in[l];
+        cudaMemset(m->W[l], 0, nw * 4);
+        cudaMemset(m->b[l], 0, m->outp[l] * 4);
+        cudaMemset(m->mW[l], 0, nw * 4);
+        cudaMemset(m->vW[l], 0, nw * 4);
+        cudaMemset(m->mb[l], 0, m->outp[l] * 4);
+        cudaMemset(m->vb[l], 0, m->outp[l] * 4);
+    }
+    cudaMemset(m->status, 0, sizeof(int));
+    rc = mlp_set_params(m, params);
+    if (rc) {
+        mlp_destroy(m);
+        return rc;
+    }
+    *out = m;
+    return MD_OK;
+}
+
+void mlp_destroy(mlp_model *m) {
+    if (!m) return;
+    cudaDeviceSynchronize();
+    for (void *p : m->ws) cudaFree(p);
+    for (void *p : m->allocs) cudaFree(p);
+    delete m;
+}
+
+int64_t mlp_param_count(mlp_model *m) {
+    if (!m) return 0;
+    int64_t n = 0;
+    for (int l = 0; l < m->nl; ++l) n += (int64_t)m->out[l] * m->in[l] + m->out[l];
+    return n;
+}
+
+int mlp_set_params(mlp_model *m, const float *params) {
+    if (!m || !params) return fail(MD_E_ARG, "mlp_set_params: NULL argument");
+    size_t off = 0;
+    for (int l = 0; l < m->nl; ++l) {
+        const size_t nw = (size_t)m->out[l] * m->in[l];
+        MD_CUDA_TRY(cudaMemcpy(m->W[l], params + off, nw * 4, cudaMemcpyDefault));   // rows >= out stay 0
+        off += nw;
+        MD_CUDA_TRY(cudaMemcpy(m->b[l], params + off, m->out[l] * 4, cudaMemcpyDefault));
+        off += m->out[l];
+    }
+    int rc = refresh_bf16(m, nullptr);
+    if (rc) return rc;
+    MD_CUDA_TRY(cudaDeviceSynchronize());
+    return MD_OK;
+}
+
+int mlp_get_params(mlp_model *m, float *params) {
+    if (!m || !params) return fail(MD_E_ARG, "mlp_get_params: NULL argument");
+    MD_CUDA_TRY(cudaDeviceSynchronize());
+    size_t off = 0;
+    for (int l = 0; l < m->nl; ++l) {
+        const size_t nw = (size_t)m->out[l] * m->in[l];
+        MD_CUDA_TRY(cudaMemcpy(params + off, m->W[l], nw * 4, cudaMemcpyDefault));
+        off += nw;
+        MD_CUDA_TRY(cudaMemcpy(params + off, m->b[l], m->out[l] * 4, cudaMemcpyDefault));
+        off += m->out[l];
+    }
+    return MD_OK;
+}
+
+int mlp_forward(mlp_model *m, const float *X, int64_t M, float *P_out, void *stream) {
+    if (!m || !X || !P_out || M < 1) return fail(MD_E_ARG, "mlp_forward: bad arguments");
+    cudaStream_t st = (cudaStream_t)stream;
+    const long long Mp = pad128(M);
+    int rc = ensure_ws(m, Mp);
+    if (rc) return rc;
+    if ((rc = forward(m, X, M, Mp, false, st))) return rc;
+    k_softmax<<<(unsigned)((M + 7) / 8), 256, 0, st>>>(m->logits, m->npad, (int)M, m->ncls, P_out,
+                                                       nullptr, nullptr, nullptr, 0, 0.f);
+    MD_CUDA_TRY(cudaGetLastError());
+    return MD_OK;
+}
+
+int mlp_grad(mlp_model *m, const float *X, const float *T, int32_t B, float *grad_out,
+             float *loss_out, void *stream) {
+    if (!m || !X || !T || B < 128 || B % 128) return fail(MD_E_ARG, "mlp_grad: batch must be a multiple of 128");
+    cudaStream_t st = (cudaStream_t)stream;
+    int rc = ensure_ws(m, B);
+    if (rc) return rc;
+    if ((rc = backward(m, X, T, B, loss_out, st))) return rc;
+    if (grad_out) {
+        size_t off = 0;
+        for (int l = 0; l < m->nl; ++l) {
+            const size_t nw = (size_t)m->out[l] * m->in[l];
+            MD_CUDA_TRY(cudaMemcpyAsync(grad_out + off, m->gW[l], nw * 4, cudaMemcpyDefault, st));
+            off += nw;
+            MD_CUDA_TRY(cudaMemcpyAsync(grad_out + off, m->gb[l], m->out[l] * 4, cudaMemcpyDefault, st));
+            off += m->out[l];
+        }
+    }
+    return MD_OK;
+}
+
+int mlp_train_step(mlp_model *m, const float *X, const float *T, int32_t B, float lr,
+                   float *loss_out, void *stream) {
+    int rc = mlp_grad(m, X, T, B, nullptr, loss_out, stream);
+    if (rc) return rc;
+    cudaStream_t st = (cudaStream_t)stream;
+    m->adam_t += 1;
+    const float b1 = 0.9f, b2 = 0.999f, eps = 1e-8f;
+    const float c1 = 1.f - powf(b1, (float)m->adam_t), c2 = 1.f - powf(b2, (float)m->adam_t);
+    for (int l = 0; l < m->nl; ++l) {
+        const int rows = m->out[l], cols = m->in[l];
+        k_adam<<<(rows * cols + 255) / 256, 256, 0, st>>>(m->W[l], m->mW[l], m->vW[l], m->gW[l], rows,
+                                                          cols, cols, lr, b1, b2, c1, c2, eps,
+                                                          l ? m->Wh[l] : nullptr,
+                                                          l ? m->Wt[l] : nullptr, m->outp[l]);
+        k_adam<<<(rows + 255) / 256, 256, 0, st>>>(m->b[l], m->mb[l], m->vb[l], m->gb[l], 1, rows, rows,
+                                                   lr, b1, b2, c1, c2, eps, nullptr, nullptr, 0);
+    }
+    MD_CUDA_TRY(cudaGetLastError());
+    return MD_OK;
+}
+
+int mlp_status(mlp_model *m) {
+    if (!m) return fail(MD_E_ARG, "mlp_status: NULL model");
+    int s = 0;
+    MD_CUDA_TRY(cudaDeviceSynchronize());
+    MD_CUDA_TRY(cudaMemcpy(&s, m->status, sizeof(int), cudaMemcpyDeviceToHost));
+    if (s) {
+        cudaMemset(m->status, 0, sizeof(int));
+        return fail(MD_E_TIMEOUT, "tensor-core GEMM wait timed out");
+    }
+    return MD_OK;
+}
+
+int bf16_gemm_tn(const void *A, const void *B, float *C, int32_t M, int32_t N, int32_t K,
+                 int32_t *status, void *stream) {
+    if (!A || !B || !C || !status) return fail(MD_E_ARG, "bf16_gemm_tn: NULL argument");
+    GemmArgs g{};
+    g.A = (const bf16 *)A;
+    g.B = (const bf16 *)B;
+    g.lda = K;
+    g.ldb = K;
+    g.M = M;
+    g.N = N;
+    g.K = K;
+    g.C = C;
+    g.ldc = N;
+    g.status = status;
+    return gemm_launch<EPI_F32>(g, (cudaStream_t)stream);
+}
+
+}  // extern "C"

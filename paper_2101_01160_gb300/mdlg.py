@@ -93,6 +93,16 @@ _SIGS = {
     "feq_wsg": ([C.c_double, C.c_double, C.c_double, C.c_double, C.c_int32, P, P], C.c_int),
     "feq_compare": ([P, P, C.c_int32, P, P], C.c_int),
     "md_last_error": ([], C.c_char_p),
+    "mlp_create": ([C.c_int32, C.c_int32, C.c_int32, P, P, P, C.POINTER(P)], C.c_int),
+    "mlp_destroy": ([P], None),
+    "mlp_param_count": ([P], C.c_int64),
+    "mlp_set_params": ([P, P], C.c_int),
+    "mlp_get_params": ([P, P], C.c_int),
+    "mlp_forward": ([P, P, C.c_int64, P, P], C.c_int),
+    "mlp_grad": ([P, P, P, C.c_int32, P, P, P], C.c_int),
+    "mlp_train_step": ([P, P, P, C.c_int32, C.c_float, P, P], C.c_int),
+    "mlp_status": ([P], C.c_int),
+    "bf16_gemm_tn": ([P, P, P, C.c_int32, C.c_int32, C.c_int32, P, P], C.c_int),
 }
 
 
@@ -329,3 +339,76 @@ def feq_compare(R, Q, stream=None):
     out = torch.empty(3, dtype=torch.float64, device="cuda")
     _check(load().feq_compare(_ptr(R), _ptr(Q), R.numel(), _ptr(out), _stream(stream)))
     return out
+
+
+# ---------------------------------------------------------------- surrogate
+SURR_SIZES = (4, 256, 256, 256, 256, 81)
+
+
+class MLP:
+    """The f_eq surrogate (mlp_create & co.).  params: packed FP32 numpy
+    vector (W_1, b_1, W_2, b_2, ...), shift/scale: feature normalisation."""
+
+    def __init__(self, params, shift, scale, n_hidden=4, width=256, n_classes=81):
+        self._params = np.ascontiguousarray(params, dtype=np.float32)
+        sh = np.ascontiguousarray(shift, dtype=np.float32)
+        sc = np.ascontiguousarray(scale, dtype=np.float32)
+        h = P()
+        _check(load().mlp_create(n_hidden, width, n_classes, _ptr(sh), _ptr(sc), _ptr(self._params),
+                                 C.byref(h)))
+        self.h = h
+        self.n_classes = n_classes
+        self.n_params = int(load().mlp_param_count(self.h))
+
+    def close(self):
+        if getattr(self, "h", None):
+            load().mlp_destroy(self.h)
+            self.h = None
+
+    __del__ = close
+
+    def get_params(self):
+        out = np.zeros(self.n_params, np.float32)
+        _check(load().mlp_get_params(self.h, _ptr(out)))
+        return out
+
+    def set_params(self, params):
+        p_ = np.ascontiguousarray(params, dtype=np.float32)
+        _check(load().mlp_set_params(self.h, _ptr(p_)))
+
+    def forward(self, X, out=None, stream=None):
+        """X: device float32 [M, 4] -> device float32 [M, n_classes]."""
+        import torch
+
+        if out is None:
+            out = torch.empty((X.shape[0], self.n_classes), dtype=torch.float32, device="cuda")
+        _check(load().mlp_forward(self.h, _ptr(X), X.shape[0], _ptr(out), _stream(stream)))
+        return out
+
+    def grad(self, X, T, stream=None):
+        import torch
+
+        g = torch.empty(self.n_params, dtype=torch.float32, device="cuda")
+        loss = torch.empty(1, dtype=torch.float32, device="cuda")
+        _check(load().mlp_grad(self.h, _ptr(X), _ptr(T), X.shape[0], _ptr(g), _ptr(loss),
+                               _stream(stream)))
+        return g, loss
+
+    def train_step(self, X, T, lr, loss=None, stream=None):
+        _check(load().mlp_train_step(self.h, _ptr(X), _ptr(T), X.shape[0], float(lr), _ptr(loss),
+                                     _stream(stream)))
+
+    def status(self):
+        _check(load().mlp_status(self.h))
+
+
+def bf16_gemm_tn(A, B, stream=None):
+    """C = A @ B.T on the tensor cores (A [M,K], B [N,K] bf16 device tensors)."""
+    import torch
+
+    M, K = A.shape
+    N = B.shape[0]
+    Cm = torch.empty((M, N), dtype=torch.float32, device="cuda")
+    st = torch.zeros(1, dtype=torch.int32, device="cuda")
+    _check(load().bf16_gemm_tn(_ptr(A), _ptr(B), _ptr(Cm), M, N, K, _ptr(st), _stream(stream)))
+    return Cm, st
