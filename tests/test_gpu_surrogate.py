@@ -98,3 +98,21 @@ def test_training_lowers_loss(mdlg, orc):
     assert losses[-1] < 0.2 * losses[0], losses
     P = m.forward(Xd).cpu().numpy()
     assert np.max(np.abs(P - T)) < 0.05
+
+
+def test_surrogate_pipeline_beats_md_free_baseline(mdlg):
+    """End to end on a reduced ensemble: MD-measured equilibria as training
+    data, tensor-core training, held-out replicas; the surrogate (no MD at
+    query time) must beat the ballistic Gaussian (the other MD-free
+    prediction) and stay within 2e-2 of every measured class."""
+    from paper_2101_01160_gb300 import surrogate
+
+    ds = surrogate.generate(31, n_rep=96, steps=8000, n_equil=2000, n_min=2048, n_max=8192)
+    tr, te = surrogate.split(ds, 0.15, seed=1)
+    assert len(tr.X) > 300 and len(te.X) > 30
+    m = surrogate.new_model(3)
+    hist = surrogate.train(m, tr, steps=3000, batch=512, log_every=500)
+    assert hist[-1][1] < 0.3 * hist[0][1], hist
+    res = surrogate.evaluate(m, te)
+    assert res["surrogate"]["median"] < res["gauss_ballistic"]["median"], res
+    assert res["surrogate"]["max"] < 2e-2, res
