@@ -304,15 +304,16 @@ int feq_compare(const double *R, const double *Q, int32_t n, double *out3, void 
 /* ---- f_eq surrogate (a project addition, not in the paper) -------------- */
 
 /* A multilayer perceptron from the state point x = (phi, T, Delta t_LG,
- * Delta x) to the probabilities of n_classes displacement classes: features
- * (x - shift)/scale, n_hidden layers of width 256 with the SiLU activation
- * (the first on CUDA cores, the others as BF16 tensor-core GEMMs with FP32
- * accumulation), a softmax output; trained on the mean Kullback-Leibler
+ * Delta x) to the probabilities of n_classes (2..112) displacement classes:
+ * features (x - shift)/scale, n_hidden (2..15) layers of width 256 with the
+ * SiLU activation, a softmax output; trained on the mean Kullback-Leibler
  * divergence (Eq. kullback_leibler) to measured distributions with Adam.
- * Weights are FP32 masters with BF16 copies for the tensor cores.  params
- * (host or device, FP32) packs W_1, b_1, W_2, b_2, ... with W_l row-major
- * [out][in]; mlp_param_count gives its length.  Device memory is owned by
- * the model (workspace grows with the largest batch seen). */
+ * Training runs layer 1 in FP32 on CUDA cores and the others as BF16
+ * tensor-core GEMMs with FP32 accumulation.  Weights are FP32 masters with
+ * BF16 copies for the tensor cores.  params (host or device, FP32) packs
+ * W_1, b_1, W_2, b_2, ... with W_l row-major [out][in]; mlp_param_count
+ * gives its length.  Device memory is owned by the model (workspace grows
+ * with the largest batch seen).  MD_E_ARG for sizes outside these ranges. */
 typedef struct mlp_model mlp_model;
 int mlp_create(int32_t n_hidden, int32_t width, int32_t n_classes, const float *shift4,
                const float *scale4, const float *params, mlp_model **out);
@@ -321,7 +322,13 @@ int64_t mlp_param_count(mlp_model *m);
 int mlp_set_params(mlp_model *m, const float *params);
 int mlp_get_params(mlp_model *m, float *params);
 
-/* P_out[M][n_classes] = model(X[M][4]); X, P_out device FP32.  Asynchronous. */
+/* P_out[M][n_classes] = model(X[M][4]); X (16-byte aligned), P_out device
+ * FP32.  One fused persistent kernel; every layer runs on the tensor cores
+ * with FP32 accumulation: layer 1 as one K = 16 product of split BF16
+ * operands (x_hi W_hi + x_lo W_hi + x_hi W_lo, relative error ~2^-16), the
+ * others BF16 x BF16; SiLU through the hardware tanh approximation (relative
+ * error ~2^-11, below the BF16 rounding of the activations).  Asynchronous
+ * on `stream`; MD_E_ARG for NULL pointers, M < 1 or misaligned X. */
 int mlp_forward(mlp_model *m, const float *X, int64_t M, float *P_out, void *stream);
 
 /* Gradient of the mean KL loss over a batch (X [B][4], targets T

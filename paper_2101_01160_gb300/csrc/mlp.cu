@@ -12,6 +12,7 @@
 // p = softmax(logits[0..81)); loss = mean D_KL(t || p).
 #include <cuda_bf16.h>
 
+#include <algorithm>
 #include <cmath>
 #include <cstring>
 #include <vector>
@@ -316,6 +317,381 @@ __global__ void k_sum(const float *a, int n, float *out) {
     if (threadIdx.x == 0) *out = s[0];
 }
 
+
+// ---------------------------------------------------------------- fused inference
+// Whole forward pass in one persistent, warp-specialised kernel over 128-row
+// tiles, two tiles in flight per CTA ("slots") so that the CUDA-core
+// epilogue of one slot overlaps the tensor-core MMAs of the other.
+//   warp 0 lane 0  producer: streams weight chunks, pre-packed in global
+//                  memory in the exact shared-memory layout, with one bulk
+//                  copy (TMA) each into a ring of F_STAGES buffers;
+//   warp 1 lane 0  MMA issuer: per (tile pair, layer, slot) waits for the
+//                  slot's activations, issues tcgen05.mma into the slot's
+//                  128 x 256 FP32 accumulator in TMEM, commits;
+//   warps 2..17    epilogue, 8 warps per slot: stage the inputs, then per
+//                  layer TMEM -> bias + SiLU -> BF16 activations written
+//                  back over the slot's tile, or after the last layer a
+//                  softmax staged in shared memory and stored coalesced.
+// Layer 1 (4 inputs) is one K = 16 MMA on split operands: with
+// x = x_hi + x_lo and W = W_hi + W_lo (BF16 parts), the A row holds
+// (x_hi, x_lo, x_hi, 0) and the B row (W_hi, W_hi, W_lo, 0), so the FP32
+// accumulator receives x_hi W_hi + x_lo W_hi + x_hi W_lo, the product up to
+// the x_lo W_lo term (relative ~2^-16).
+// A warp may read only the TMEM lanes 32 (warp mod 4) .. +31, so epilogue
+// warp w serves rows 32 (w mod 4) + lane and one half of the columns.
+// Every wait is bounded; a wait that gives up sets the status flag and the
+// roles wind down (uniformly within a slot) instead of hanging.
+constexpr int FK = 64;                     // features per weight chunk
+constexpr int F_STAGES = 3;
+constexpr int F_SBO_A = 256 / 8 * 128;     // 8-row groups of the 256-wide activation tile
+constexpr int F_SBO_B = FK / 8 * 128;      // 8-row groups of a weight chunk
+constexpr int F_SBO_B0 = 16 / 8 * 128;     // 8-row groups of the K = 16 layer-1 operand
+constexpr int F_CHUNK_BYTES = 256 * FK * 2;
+constexpr int F_MAXL = 15;
+constexpr int F_EPI_WARPS = 8;             // per slot
+constexpr int F_THREADS = (2 + 2 * F_EPI_WARPS) * 32;
+constexpr int F_ACT_BYTES = 128 * 256 * 2;
+constexpr int F_RED_OFF = 60 * 1024;       // softmax partials inside a slot's tile
+constexpr int MLP_MAX_CLASSES = 112;       // FP32 stage rows must end below them
+
+struct FusedArgs {
+    const float *X;
+    long long M;
+    float *P;
+    int ncls;
+    float4 shift, scale;
+    const bf16 *Wp[F_MAXL + 1];    // packed operand of every layer (layer 0: split K = 16)
+    const float *bh[F_MAXL + 1];   // biases
+    int nt;                        // layers; the last one is the output
+    int p_aligned;                 // P 16-byte aligned: output tiles by bulk copy
+    int *status;
+};
+
+__device__ __forceinline__ int act_off(int r, int k) {
+    return (r >> 3) * F_SBO_A + (k >> 3) * 128 + (r & 7) * 16 + (k & 7) * 2;
+}
+
+// silu(z) = z sigmoid(z) = h + h tanh(h), h = z / 2: one special-function
+// operation (tanh.approx, relative error about 2^-11, below the BF16 rounding
+// of the stored activation).
+__device__ __forceinline__ float silu_fast(float z) {
+    const float h = 0.5f * z;
+    float t;
+    asm("tanh.approx.f32 %0, %1;" : "=f"(t) : "f"(h));
+    return fmaf(h, t, h);
+}
+
+__device__ __forceinline__ uint32_t pack_bf16(float lo, float hi) {
+    __nv_bfloat162 v = __floats2bfloat162_rn(lo, hi);
+    return *reinterpret_cast<uint32_t *>(&v);
+}
+
+__device__ __forceinline__ int layer_chunks(int l) { return l == 0 ? 1 : 256 / FK; }
+
+__global__ void __launch_bounds__(F_THREADS, 1) k_mlp_fused(FusedArgs a) {
+    extern __shared__ __align__(1024) unsigned char sm[];
+    unsigned char *ring = sm + 2 * F_ACT_BYTES;
+    uint64_t *full = reinterpret_cast<uint64_t *>(ring + F_STAGES * F_CHUNK_BYTES);
+    uint64_t *empty = full + F_STAGES;
+    uint64_t *accf = empty + F_STAGES;     // per slot: accumulator complete
+    uint64_t *actr = accf + 2;             // per slot: activations written, TMEM read
+    uint32_t *s_tmem = reinterpret_cast<uint32_t *>(actr + 2);
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    if (warp == 1) umma::tmem_alloc(s_tmem, 512);
+    if (tid == 0) {
+        for (int i = 0; i < F_STAGES; ++i) {
+            umma::mbar_init(&full[i], 1);
+            umma::mbar_init(&empty[i], 1);
+        }
+        for (int i = 0; i < 2; ++i) {
+            umma::mbar_init(&accf[i], 1);
+            umma::mbar_init(&actr[i], 32 * F_EPI_WARPS);
+        }
+        umma::mbar_fence_init();
+    }
+    umma::fence_before();
+    __syncthreads();
+    umma::fence_after();
+    const uint32_t tmem = *s_tmem;
+    const long long ntiles = (a.M + 127) / 128;
+    const long long my_tiles = ntiles > blockIdx.x ? (ntiles - blockIdx.x + gridDim.x - 1) / gridDim.x : 0;
+    const long long npairs = (my_tiles + 1) / 2;
+    const int nt = a.nt;
+    bool bad = false;
+
+    if (warp == 0) {
+        // ------------------------------------------------ producer
+        if (lane == 0) {
+            int st = 0;
+            uint32_t ph = 0;          // phase of the ring pass that stage st is in
+            long long c = 0;          // chunks issued
+            for (long long p = 0; p < npairs && !bad; ++p)
+                for (int l = 0; l < nt && !bad; ++l)
+                    for (int s = 0; s < 2 && !bad; ++s) {
+                        if (2 * p + s >= my_tiles) continue;
+                        const int N = l == nt - 1 ? 128 : 256, K = l == 0 ? 16 : FK;
+                        const uint32_t bytes = (uint32_t)(N * K * 2);
+                        for (int kc = 0; kc < layer_chunks(l); ++kc, ++c) {
+                            // from the second pass on, wait until the MMAs of
+                            // the previous pass have released the stage
+                            if (c >= F_STAGES && !umma::mbar_wait(&empty[st], ph ^ 1u, GEMM_WAIT_NS)) {
+                                bad = true;
+                                break;
+                            }
+                            umma::mbar_expect_tx(&full[st], bytes);
+                            umma::bulk_g2s(ring + st * F_CHUNK_BYTES, a.Wp[l] + (size_t)kc * N * K, bytes,
+                                           &full[st]);
+                            if (++st == F_STAGES) {
+                                st = 0;
+                                ph ^= 1u;
+                            }
+                        }
+                    }
+            // every copy issued must have landed before the CTA exits: the
+            // last min(c, F_STAGES) chunks, walking the ring backwards
+            for (long long i = 0; i < c && i < F_STAGES; ++i) {
+                if (--st < 0) {
+                    st = F_STAGES - 1;
+                    ph ^= 1u;
+                }
+                if (!umma::mbar_wait(&full[st], ph, GEMM_WAIT_NS)) bad = true;
+            }
+            if (bad) atomicOr(a.status, 1);
+        }
+        __syncwarp();
+    } else if (warp == 1) {
+        // ------------------------------------------------ MMA issuer
+        if (lane == 0) {
+            int st = 0;
+            uint32_t ph = 0;
+            long long c = 0;          // chunks consumed
+            int last_st = 0;
+            uint32_t last_ph = 0;
+            const uint64_t ring_desc = umma::desc(umma::saddr(ring), 128, F_SBO_B);
+            const uint64_t ring_desc0 = umma::desc(umma::saddr(ring), 128, F_SBO_B0);
+            uint32_t kpar[2] = {0u, 0u};   // per slot: parity of the next actr phase
+            for (long long p = 0; p < npairs && !bad; ++p)
+                for (int l = 0; l < nt && !bad; ++l)
+                    for (int s = 0; s < 2 && !bad; ++s) {
+                        if (2 * p + s >= my_tiles) continue;
+                        if (!umma::mbar_wait(&actr[s], kpar[s], GEMM_WAIT_NS)) {
+                            bad = true;
+                            break;
+                        }
+                        kpar[s] ^= 1u;
+                        umma::fence_after();
+                        const uint32_t idesc = umma::idesc_bf16(128, l == nt - 1 ? 128 : 256);
+                        const uint64_t act_desc = umma::desc(umma::saddr(sm + s * F_ACT_BYTES), 128, F_SBO_A);
+                        const uint32_t d = tmem + (uint32_t)(s * 256);
+                        for (int kc = 0; kc < layer_chunks(l); ++kc, ++c) {
+                            if (!umma::mbar_wait(&full[st], ph, GEMM_WAIT_NS)) {
+                                bad = true;
+                                break;
+                            }
+                            umma::fence_after();
+                            const uint64_t bdesc = (l == 0 ? ring_desc0 : ring_desc) + (uint64_t)((st * F_CHUNK_BYTES) >> 4);
+                            if (l == 0) {
+                                umma::mma(d, act_desc, bdesc, idesc, 0u);
+                            } else {
+                                const uint64_t adesc = act_desc + (uint64_t)((kc * (FK / 8) * 128) >> 4);
+#pragma unroll
+                                for (int k4 = 0; k4 < FK / 16; ++k4)
+                                    umma::mma(d, adesc + (uint64_t)(k4 * 16), bdesc + (uint64_t)(k4 * 16), idesc,
+                                              (kc | k4) ? 1u : 0u);
+                            }
+                            umma::commit(&empty[st]);
+                            last_st = st;
+                            last_ph = ph;
+                            if (++st == F_STAGES) {
+                                st = 0;
+                                ph ^= 1u;
+                            }
+                        }
+                        if (!bad) umma::commit(&accf[s]);
+                    }
+            // the last MMAs must be complete before TMEM is released
+            if (c > 0 && !umma::mbar_wait(&empty[last_st], last_ph, GEMM_WAIT_NS)) bad = true;
+            if (bad) atomicOr(a.status, 1);
+        }
+        __syncwarp();
+    } else {
+        // ------------------------------------------------ epilogue slots
+        const int e = warp - 2, s = e / F_EPI_WARPS, half = (e / 4) & 1, quad = warp & 3;
+        const int r = quad * 32 + lane, bar_id = 1 + s, nthr = 32 * F_EPI_WARPS;
+        const int ew = e % F_EPI_WARPS, ts = ew * 32 + lane;   // warp / thread index within the slot
+        unsigned char *act = sm + s * F_ACT_BYTES;
+        float *stage = reinterpret_cast<float *>(act);
+        float *red = reinterpret_cast<float *>(act + F_RED_OFF);   // [max, sum][2 halves][128 rows]
+        const uint32_t trow = tmem + (uint32_t)(s * 256) + ((uint32_t)(quad * 32) << 16);
+        const int ncls = a.ncls;
+        const int hs = (ncls + 31) / 32 * 16;                   // softmax columns per half
+        const int cbeg = half * hs, cend = min(cbeg + hs, ncls);
+        uint32_t kpar = 0u;                                     // parity of the next accf phase
+        for (long long p = 0; p < npairs; ++p) {
+            const long long j = 2 * p + s;
+            if (j >= my_tiles) break;
+            const long long m0 = (blockIdx.x + j * gridDim.x) * 128;
+            // ---- inputs: split (x_hi, x_lo, x_hi, 0) rows of the K = 16 operand
+            if (half == 0) {
+                uint4 u0 = make_uint4(0, 0, 0, 0), u1 = u0;
+                if (m0 + r < a.M) {
+                    const float4 x = __ldg(reinterpret_cast<const float4 *>(a.X) + m0 + r);
+                    const float f0 = (x.x - a.shift.x) / a.scale.x, f1 = (x.y - a.shift.y) / a.scale.y;
+                    const float f2 = (x.z - a.shift.z) / a.scale.z, f3 = (x.w - a.shift.w) / a.scale.w;
+                    const __nv_bfloat162 h01 = __floats2bfloat162_rn(f0, f1), h23 = __floats2bfloat162_rn(f2, f3);
+                    const float2 g01 = __bfloat1622float2(h01), g23 = __bfloat1622float2(h23);
+                    u0.x = *reinterpret_cast<const uint32_t *>(&h01);
+                    u0.y = *reinterpret_cast<const uint32_t *>(&h23);
+                    u0.z = pack_bf16(f0 - g01.x, f1 - g01.y);
+                    u0.w = pack_bf16(f2 - g23.x, f3 - g23.y);
+                    u1.x = u0.x;
+                    u1.y = u0.y;
+                }
+                *reinterpret_cast<uint4 *>(act + act_off(r, 0)) = u0;
+                *reinterpret_cast<uint4 *>(act + act_off(r, 8)) = u1;
+                umma::fence_proxy_smem();
+            }
+            umma::mbar_arrive(&actr[s]);
+            // ---- layers
+            for (int l = 0; l < nt && !bad; ++l) {
+                const bool ok = umma::mbar_wait(&accf[s], kpar, GEMM_WAIT_NS);
+                kpar ^= 1u;
+                if (!umma::bar_and(bar_id, nthr, ok)) {
+                    bad = true;
+                    break;
+                }
+                umma::fence_after();
+                const float *bias = a.bh[l];
+                if (l < nt - 1) {
+                    // 8 groups of 16 columns; the TMEM load of group g + 1 is
+                    // in flight while group g is computed
+                    const int cb = half * 128;
+                    uint32_t v[2][16];
+                    umma::ld16_async(trow + (uint32_t)cb, v[0]);
+                    umma::wait_ld(v[0]);
+#pragma unroll
+                    for (int g = 0; g < 8; ++g) {
+                        const int cur = g & 1, nxt = cur ^ 1;
+                        if (g < 7) umma::ld16_async(trow + (uint32_t)(cb + 16 * (g + 1)), v[nxt]);
+                        float4 bq[4];
+#pragma unroll
+                        for (int i = 0; i < 4; ++i) bq[i] = __ldg(reinterpret_cast<const float4 *>(bias + cb + 16 * g) + i);
+                        const float *bb = reinterpret_cast<const float *>(bq);
+                        uint32_t hv[8];
+#pragma unroll
+                        for (int i = 0; i < 8; ++i)
+                            hv[i] = pack_bf16(silu_fast(__uint_as_float(v[cur][2 * i]) + bb[2 * i]),
+                                              silu_fast(__uint_as_float(v[cur][2 * i + 1]) + bb[2 * i + 1]));
+                        *reinterpret_cast<uint4 *>(act + act_off(r, cb + 16 * g)) = make_uint4(hv[0], hv[1], hv[2], hv[3]);
+                        *reinterpret_cast<uint4 *>(act + act_off(r, cb + 16 * g + 8)) = make_uint4(hv[4], hv[5], hv[6], hv[7]);
+                        if (g < 7) umma::wait_ld(v[nxt]);
+                    }
+                    umma::fence_before();
+                    umma::fence_proxy_smem();
+                    umma::mbar_arrive(&actr[s]);
+                } else {
+                    // softmax: each half takes columns [cbeg, cend); row
+                    // maxima and sums are combined through shared memory; the
+                    // normalised rows are staged densely (stride ncls) over
+                    // the slot's tile, which is then one contiguous block of
+                    // P, written by a single bulk copy (TMA)
+                    float mx = -INFINITY;
+                    for (int c0 = cbeg; c0 < cend; c0 += 16) {
+                        uint32_t v[16];
+                        umma::ld16_async(trow + (uint32_t)c0, v);
+                        float4 b4[4];
+#pragma unroll
+                        for (int i = 0; i < 4; ++i) b4[i] = __ldg(reinterpret_cast<const float4 *>(bias + c0) + i);
+                        const float *bb = reinterpret_cast<const float *>(b4);
+                        umma::wait_ld(v);
+#pragma unroll
+                        for (int i = 0; i < 16; ++i)
+                            if (c0 + i < cend) mx = fmaxf(mx, __uint_as_float(v[i]) + bb[i]);
+                    }
+                    red[half * 128 + r] = mx;
+                    umma::bar_sync(bar_id, nthr);
+                    mx = fmaxf(red[r], red[128 + r]);
+                    float sum = 0.f;
+                    for (int c0 = cbeg; c0 < cend; c0 += 16) {
+                        uint32_t v[16];
+                        umma::ld16_async(trow + (uint32_t)c0, v);
+                        float4 b4[4];
+#pragma unroll
+                        for (int i = 0; i < 4; ++i) b4[i] = __ldg(reinterpret_cast<const float4 *>(bias + c0) + i);
+                        const float *bb = reinterpret_cast<const float *>(b4);
+                        umma::wait_ld(v);
+#pragma unroll
+                        for (int i = 0; i < 16; ++i)
+                            if (c0 + i < cend) {
+                                const float ez = __expf(__uint_as_float(v[i]) + bb[i] - mx);
+                                sum += ez;
+                                stage[r * ncls + c0 + i] = ez;
+                            }
+                    }
+                    umma::fence_before();
+                    red[256 + half * 128 + r] = sum;
+                    umma::bar_sync(bar_id, nthr);
+                    const float inv = 1.0f / (red[256 + r] + red[384 + r]);
+                    for (int c = cbeg; c < cend; ++c) stage[r * ncls + c] *= inv;
+                    umma::fence_proxy_smem();
+                    umma::bar_sync(bar_id, nthr);
+                    if (ts == 0) {
+                        const long long rows = a.M - m0 < 128 ? a.M - m0 : 128;
+                        const uint32_t n = (uint32_t)rows * (uint32_t)ncls, n4 = n & ~3u;
+                        float *dst = a.P + (size_t)m0 * ncls;
+                        if (a.p_aligned) {
+                            if (n4) umma::bulk_s2g(dst, stage, n4 * 4);
+                            umma::bulk_commit();
+                            for (uint32_t i = n4; i < n; ++i) dst[i] = stage[i];
+                            umma::bulk_wait_read();
+                        } else {
+                            for (uint32_t i = 0; i < n; ++i) dst[i] = stage[i];
+                        }
+                    }
+                    umma::bar_sync(bar_id, nthr);    // the next tile's inputs overwrite the stage
+                }
+            }
+            if (bad) break;
+        }
+        if (ts == 0) {
+            umma::bulk_wait();              // the output rows have reached global memory
+            if (bad) atomicOr(a.status, 1);
+        }
+    }
+    umma::fence_before();
+    __syncthreads();
+    if (warp == 1) umma::tmem_free(tmem, 512);
+}
+
+constexpr size_t FUSED_SMEM = 2 * F_ACT_BYTES + F_STAGES * F_CHUNK_BYTES + (2 * F_STAGES + 4) * 8 + 16;
+static_assert(FUSED_SMEM <= 232448, "fused MLP shared memory above 227 KB");
+static_assert(128 * MLP_MAX_CLASSES * 4 <= F_RED_OFF && F_RED_OFF + 4 * 128 * 4 <= F_ACT_BYTES,
+              "softmax stage overlaps the partials");
+
+// Packs layer 1, W [256][4] FP32, into the split K = 16 operand
+// (W_hi, W_hi, W_lo, 0) in the shared-memory layout.
+__global__ void k_pack0(const float *W, bf16 *out) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= 256 * 16) return;
+    const int n = i / 16, k = i % 16;
+    float v = 0.f;
+    if (k < 12) {
+        const float w = W[n * 4 + (k & 3)];
+        const float hi = __bfloat162float(__float2bfloat16_rn(w));
+        v = k < 8 ? hi : w - hi;
+    }
+    out[(n >> 3) * (F_SBO_B0 / 2) + (k >> 3) * 64 + (n & 7) * 8 + (k & 7)] = __float2bfloat16_rn(v);
+}
+
+// Packs W [N][256] (BF16 row-major) into 64-feature chunks laid out exactly
+// as the fused kernel's shared-memory weight buffer.
+__global__ void k_pack(const bf16 *W, int N, bf16 *out) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= N * 256) return;
+    const int n = i / 256, k = i % 256, kc = k / FK, kk = k % FK;
+    out[(size_t)kc * N * FK + (n >> 3) * (F_SBO_B / 2) + (kk >> 3) * 64 + (n & 7) * 8 + (kk & 7)] = W[i];
+}
+
 }  // namespace mdlg
 
 using namespace mdlg;
@@ -329,6 +705,8 @@ struct mlp_model {
     // FP32 master, Adam moments, gradients: per layer W [outp][in], b [outp]
     std::vector<float *> W, b, mW, vW, mb, vb, gW, gb;
     std::vector<bf16 *> Wh, Wt;   // BF16 [outp][in] and [in][outp] (layers >= 1)
+    std::vector<bf16 *> Wp;       // chunk-packed copies for the fused forward pass
+    bool packed = false;
     int adam_t = 0;
     // workspace
     long long cap = 0;            // rows
@@ -380,6 +758,7 @@ int ensure_ws(mlp_model *m, long long rows) {
 }
 
 int refresh_bf16(mlp_model *m, cudaStream_t st) {
+    m->packed = false;
     for (int l = 1; l < m->nl; ++l) {
         const int n = m->outp[l] * m->in[l];
         k_to_bf16<<<(n + 255) / 256, 256, 0, st>>>(m->W[l], n, m->Wh[l]);
@@ -492,7 +871,6 @@ int backward(mlp_model *m, const float *X, const float *T, int Mb, float *loss_d
     return MD_OK;
 }
 
-long long pad128(long long M) { return (M + 127) / 128 * 128; }
 
 }  // namespace
 
@@ -501,8 +879,8 @@ extern "C" {
 int mlp_create(int32_t n_hidden, int32_t width, int32_t n_classes, const float *shift4,
                const float *scale4, const float *params, mlp_model **out) {
     if (!out || !shift4 || !scale4 || !params || n_hidden < 2 || n_hidden > 15 || width != 256 ||
-        n_classes < 2 || n_classes > 128)
-        return fail(MD_E_ARG, "mlp_create: n_hidden in [2,15], width 256, classes in [2,128]");
+        n_classes < 2 || n_classes > MLP_MAX_CLASSES)
+        return fail(MD_E_ARG, "mlp_create: n_hidden in [2,15], width 256, classes in [2,112]");
     mlp_model *m = new mlp_model();
     m->nl = n_hidden + 1;
     m->width = width;
@@ -523,6 +901,7 @@ int mlp_create(int32_t n_hidden, int32_t width, int32_t n_classes, const float *
     m->b = m->mW = m->vW = m->mb = m->vb = m->gW = m->gb = m->W;
     m->Wh.assign(m->nl, nullptr);
     m->Wt.assign(m->nl, nullptr);
+    m->Wp.assign(m->nl, nullptr);
     for (int l = 0; l < m->nl; ++l) {
         const size_t nw = (size_t)m->outp[l] * m->in[l], nbias = (size_t)m->outp[l];
         A((void **)&m->W[l], nw * 4);
@@ -536,6 +915,9 @@ int mlp_create(int32_t n_hidden, int32_t width, int32_t n_classes, const float *
         if (l > 0) {
             A((void **)&m->Wh[l], nw * 2);
             A((void **)&m->Wt[l], nw * 2);
+            A((void **)&m->Wp[l], nw * 2);
+        } else {
+            A((void **)&m->Wp[0], (size_t)m->outp[0] * 16 * 2);
         }
     }
     A((void **)&m->status, sizeof(int));
@@ -609,13 +991,41 @@ int mlp_get_params(mlp_model *m, float *params) {
 
 int mlp_forward(mlp_model *m, const float *X, int64_t M, float *P_out, void *stream) {
     if (!m || !X || !P_out || M < 1) return fail(MD_E_ARG, "mlp_forward: bad arguments");
+    if ((uintptr_t)X & 15) return fail(MD_E_ARG, "mlp_forward: X must be 16-byte aligned");
     cudaStream_t st = (cudaStream_t)stream;
-    const long long Mp = pad128(M);
-    int rc = ensure_ws(m, Mp);
-    if (rc) return rc;
-    if ((rc = forward(m, X, M, Mp, false, st))) return rc;
-    k_softmax<<<(unsigned)((M + 7) / 8), 256, 0, st>>>(m->logits, m->npad, (int)M, m->ncls, P_out,
-                                                       nullptr, nullptr, nullptr, 0, 0.f);
+    if (!m->packed) {
+        k_pack0<<<16, 256, 0, st>>>(m->W[0], m->Wp[0]);
+        for (int l = 1; l < m->nl; ++l) {
+            const int n = m->outp[l] * 256;
+            k_pack<<<(n + 255) / 256, 256, 0, st>>>(m->Wh[l], m->outp[l], m->Wp[l]);
+        }
+        MD_CUDA_TRY(cudaGetLastError());
+        m->packed = true;
+    }
+    FusedArgs a{};
+    a.X = X;
+    a.M = M;
+    a.P = P_out;
+    a.ncls = m->ncls;
+    a.shift = make_float4(m->shift[0], m->shift[1], m->shift[2], m->shift[3]);
+    a.scale = make_float4(m->scale[0], m->scale[1], m->scale[2], m->scale[3]);
+    a.nt = m->nl;
+    for (int l = 0; l < m->nl; ++l) {
+        a.Wp[l] = m->Wp[l];
+        a.bh[l] = m->b[l];
+    }
+    a.p_aligned = ((uintptr_t)P_out & 15) == 0;
+    a.status = m->status;
+    static int nsm = 0;
+    if (!nsm) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    }
+    MD_CUDA_TRY(cudaFuncSetAttribute(k_mlp_fused, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)FUSED_SMEM));
+    const long long tiles = (M + 127) / 128;
+    const int grid = (int)std::min<long long>(tiles, nsm);
+    k_mlp_fused<<<grid, F_THREADS, FUSED_SMEM, st>>>(a);
     MD_CUDA_TRY(cudaGetLastError());
     return MD_OK;
 }
@@ -646,6 +1056,7 @@ int mlp_train_step(mlp_model *m, const float *X, const float *T, int32_t B, floa
     if (rc) return rc;
     cudaStream_t st = (cudaStream_t)stream;
     m->adam_t += 1;
+    m->packed = false;
     const float b1 = 0.9f, b2 = 0.999f, eps = 1e-8f;
     const float c1 = 1.f - powf(b1, (float)m->adam_t), c2 = 1.f - powf(b2, (float)m->adam_t);
     for (int l = 0; l < m->nl; ++l) {
