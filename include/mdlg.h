@@ -273,6 +273,22 @@ int feq_batch(md_system *s, int32_t lg, int32_t dxi, int32_t symmetrize, double 
 int mdlg_bin(const md_snapshot *t0, const md_snapshot *t1, int64_t n, int32_t lx, int32_t W,
              int32_t *hist_out, int64_t *overflow_out, double *mom_out, void *stream);
 
+/* mdlg_bin without any device allocation (the paper has no counterpart:
+ * this is a library convenience for callers that must not allocate, e.g.
+ * inside a memory-pool-free loop).  Same arguments, same results bit for
+ * bit (same launch shape).  The per-CTA moment partials go to one fixed
+ * 32 KiB device array inside the library, room for 2048 CTAs; the grid is
+ * min(ceil(n/256), 8 x SM count), 1216 CTAs on a 152-SM GPU, and a call
+ * that would need more returns MD_E_LIMIT.  The outputs are cleared with
+ * cudaMemsetAsync on `stream`; the array needs no clearing.  The array is
+ * shared by every call on a device: calls that may run at the same time on
+ * the device (other streams, other host threads, without ordering between
+ * them) race on it and can return wrong moments, so order them.  The first
+ * call on each device looks up the array's address (cudaGetSymbolAddress);
+ * make that first call before any stream capture. */
+int mdlg_bin_noalloc(const md_snapshot *t0, const md_snapshot *t1, int64_t n, int32_t lx, int32_t W,
+                     int32_t *hist_out, int64_t *overflow_out, double *mom_out, void *stream);
+
 /* ---- analytic equilibria (Sec. 3) ---------------------------------------- */
 
 /* Single-Gaussian equilibrium, Eqs. (feq_prod), (feq_gaussian): P_out[i] =

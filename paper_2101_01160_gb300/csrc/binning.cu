@@ -130,6 +130,13 @@ int bin_launch(const md_snapshot *t0, const md_snapshot *t1, int64_t n, int32_t 
     return MD_OK;
 }
 
+// Moment partials of mdlg_bin_noalloc: a fixed device array instead of a
+// per-call allocation (2 doubles per CTA, room for BIN_SCRATCH_CTAS CTAs,
+// 32 KiB).  Every CTA of a launch overwrites its own two entries and the
+// reduction reads only the first `grid`, so it never needs clearing.
+constexpr int BIN_SCRATCH_CTAS = 2048;
+static __device__ __align__(256) double g_bin_scratch[2 * BIN_SCRATCH_CTAS];
+
 int bin_grid(int64_t n) {
     static int nsm = 0;
     if (nsm == 0) {
@@ -166,4 +173,34 @@ extern "C" int mdlg_bin(const md_snapshot *t0, const md_snapshot *t1, int64_t n,
     if (rc) return rc;
     if (e != cudaSuccess) return fail(MD_E_CUDA, "mdlg_bin: cudaFreeAsync: %s", cudaGetErrorString(e));
     return MD_OK;
+}
+
+// Same computation as mdlg_bin with the partials in g_bin_scratch.  The
+// array's device address is looked up once per device; nothing is allocated.
+extern "C" int mdlg_bin_noalloc(const md_snapshot *t0, const md_snapshot *t1, int64_t n, int32_t lx,
+                                int32_t W, int32_t *hist_out, int64_t *overflow_out, double *mom_out,
+                                void *stream) {
+    int rc = bin_check_args(t0, t1, n, lx, W, hist_out, overflow_out, mom_out);
+    if (rc) return rc;
+    const int grid = bin_grid(n);
+    if (grid > BIN_SCRATCH_CTAS)
+        return fail(MD_E_LIMIT, "mdlg_bin_noalloc: %d CTAs exceed the scratch capacity of %d", grid,
+                    BIN_SCRATCH_CTAS);
+    constexpr int MAX_DEV = 64;
+    static double *scratch[MAX_DEV] = {};
+    int dev = 0;
+    MD_CUDA_TRY(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= MAX_DEV) return fail(MD_E_LIMIT, "mdlg_bin_noalloc: device %d >= %d", dev, MAX_DEV);
+    if (!scratch[dev]) {
+        double *p = nullptr;
+        const cudaError_t e = cudaGetSymbolAddress((void **)&p, g_bin_scratch);
+        if (e != cudaSuccess)
+            return fail(MD_E_CUDA, "mdlg_bin_noalloc: cudaGetSymbolAddress: %s", cudaGetErrorString(e));
+        scratch[dev] = p;
+    }
+    cudaStream_t st = (cudaStream_t)stream;
+    const int nb = (2 * W + 1) * (2 * W + 1);
+    MD_CUDA_TRY(cudaMemsetAsync(hist_out, 0, nb * sizeof(int32_t), st));
+    MD_CUDA_TRY(cudaMemsetAsync(overflow_out, 0, sizeof(int64_t), st));
+    return bin_launch(t0, t1, n, lx, W, hist_out, overflow_out, mom_out, scratch[dev], grid, st);
 }

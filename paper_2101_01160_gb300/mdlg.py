@@ -88,6 +88,8 @@ _SIGS = {
     "feq_batch": ([P, C.c_int32, C.c_int32, C.c_int32, P], C.c_int),
     "mdlg_bin": ([C.POINTER(md_snapshot), C.POINTER(md_snapshot), C.c_int64, C.c_int32, C.c_int32,
                   P, P, P, P], C.c_int),
+    "mdlg_bin_noalloc": ([C.POINTER(md_snapshot), C.POINTER(md_snapshot), C.c_int64, C.c_int32,
+                          C.c_int32, P, P, P, P], C.c_int),
     "feq_gaussian": ([C.c_double, C.c_double, C.c_double, C.c_int32, P, P], C.c_int),
     "wsg_lambda": ([C.c_double, C.c_double, C.c_int32, P, P], C.c_int),
     "feq_wsg": ([C.c_double, C.c_double, C.c_double, C.c_double, C.c_int32, P, P], C.c_int),
@@ -291,8 +293,10 @@ def feq_batch(system, lg=0, dxi=0, symmetrize=True, out=None):
     return buf[:, :nb], buf[:, nb:2 * nb], buf[:, 2 * nb:3 * nb], buf[:, 3 * nb:]
 
 
-def mdlg_bin(cell0, ox0, oy0, cell1, ox1, oy1, ncell, h, lx, W, stream=None):
-    """Histogram of lattice displacements between two device snapshots."""
+def mdlg_bin(cell0, ox0, oy0, cell1, ox1, oy1, ncell, h, lx, W, stream=None, noalloc=False):
+    """Histogram of lattice displacements between two device snapshots.
+    noalloc=True calls mdlg_bin_noalloc (library-owned scratch; the outputs
+    are still allocated here by torch)."""
     import torch
 
     f64 = int(ox0.dtype == torch.float64)
@@ -302,8 +306,9 @@ def mdlg_bin(cell0, ox0, oy0, cell1, ox1, oy1, ncell, h, lx, W, stream=None):
     hist = torch.empty(nb, dtype=torch.int32, device="cuda")
     ovf = torch.empty(1, dtype=torch.int64, device="cuda")
     mom = torch.empty(2, dtype=torch.float64, device="cuda")
-    _check(load().mdlg_bin(C.byref(s0), C.byref(s1), cell0.numel(), lx, W, _ptr(hist),
-                           _ptr(ovf), _ptr(mom), _stream(stream)))
+    fn = load().mdlg_bin_noalloc if noalloc else load().mdlg_bin
+    _check(fn(C.byref(s0), C.byref(s1), cell0.numel(), lx, W, _ptr(hist), _ptr(ovf), _ptr(mom),
+              _stream(stream)))
     return hist, ovf, mom
 
 
