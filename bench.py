@@ -50,13 +50,13 @@ N1, PHI1, T1 = 262_144, 0.0784, 20.0
 LG1, DX1 = (100, 200, 400, 1000, 2000), (0.5, 1.0, 2.0)
 
 
-def _peaks():
+def _peaks(key="hbm_gbs", fallback=6800.0):
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
             d = json.load(f)
-        return float(d["hbm_gbs"]), "measured"
+        return float(d[key]), "measured"
     except Exception:
-        return 6800.0, "fallback"
+        return fallback, "fallback"
 
 
 def _profile_traffic():
@@ -177,6 +177,67 @@ def _time_variant(mdlg, torch, params, st, md_steps, reps=3):
     return {"value": params.n * md_steps / (m * 1e-3), "ms_per_launch": m, "md_steps": md_steps}
 
 
+def _time_surrogate(mdlg, torch, n=1 << 20, reps=5):
+    """Fused f_eq-surrogate forward pass (4 -> 256 x4 SiLU -> 81 softmax,
+    BF16 tensor cores) on n query points; random-initialised weights of the
+    trained architecture (the flop count does not depend on the values)."""
+    from paper_2101_01160_gb300 import inputs, surrogate
+
+    model = surrogate.new_model(0)
+    X = torch.from_numpy(inputs.surrogate_queries(n, 3, lo=(0.02, 1.0, 0.05, 1.0),
+                                                  hi=(0.30, 20.0, 0.2, 4.0))).cuda()
+    out = torch.empty((n, model.n_classes), dtype=torch.float32, device="cuda")
+    for _ in range(3):
+        model.forward(X, out=out)
+    torch.cuda.synchronize()
+    ms = []
+    for _ in range(reps):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        model.forward(X, out=out)
+        e1.record()
+        torch.cuda.synchronize()
+        ms.append(e0.elapsed_time(e1))
+    model.status()
+    m = float(np.median(ms))
+    sizes = mdlg.SURR_SIZES
+    flop = 2.0 * sum(a * b for a, b in zip(sizes[:-1], sizes[1:])) * n
+    peak, kind = _peaks("bf16_tflops", 1900.0)
+    tf = flop / (m * 1e-3) / 1e12
+    return {"queries": n, "ms_per_launch": m, "queries_per_s": n / (m * 1e-3), "tflops": tf,
+            "bf16_peak_tflops": peak, "peak_kind": kind, "frac": tf / peak,
+            "kernel": "k_mlp_fused", "workload": "1,048,576 queries uniform in the training box"}
+
+
+def run_profile_case(args):
+    """Small cases for ncu captures (not a bench line): md64 = the first 64
+    replicas of the batched ensemble (about 1.5M particles, > L2), fixed
+    launch shape (256 threads, 1 chunk per thread, global staging), two
+    400-step warm-up launches then three 100-step launches; mlp = three fused
+    surrogate forward passes on 1M queries."""
+    import torch
+
+    from paper_2101_01160_gb300 import mdlg
+
+    mdlg.load()
+    if args.profile_case == "md64":
+        ens = ensemble(reps=range(64))
+        cat = [np.concatenate([getattr(e[4], f) for e in ens]) for f in ("x", "y", "vx", "vy")]
+        s = mdlg.System(_ens_params(mdlg, ens, mdlg.MD_FP32_CELLOFF), *cat)
+        s.tune(256, 1, 2)
+        for _ in range(2):
+            s.step(MD_PER_STEP)
+        for _ in range(3):
+            s.step(100)
+        s.sync()
+        print(json.dumps({"profile_case": "md64", "n_particles": int(sum(e[0] for e in ens)),
+                          "rebuilds": int(s.info().n_rebuilds)}))
+        s.close()
+    else:
+        r = _time_surrogate(mdlg, torch, reps=3)
+        print(json.dumps({"profile_case": "mlp", **r}))
+
+
 def run_ours(args):
     import torch
 
@@ -267,6 +328,7 @@ def run_ours(args):
             variants[name]["workload"] = ("N=262144 phi=0.0784 T=20, dt_lg {0.05..1.0} x dx "
                                           "{0.5,1,2}, one 2000-step launch")
         variants["batched_fp32_over_plain_fp64"] = (value / ws) / variants["plain_fp64"]["value"]
+        variants["surrogate_inference"] = _time_surrogate(mdlg, torch)
 
     peak, peak_kind = _peaks()
     kern_avg_s = (sum(kern_ms) / len(kern_ms)) * 1e-3
@@ -360,7 +422,12 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-variants", action="store_true")
+    ap.add_argument("--profile-case", choices=["md64", "mlp"], default=None,
+                    help="run a small case for ncu captures instead of the bench")
     args = ap.parse_args()
+    if args.profile_case:
+        run_profile_case(args)
+        return
     if args.warmup < 3:
         args.warmup = 3
     if args.impl == "reference":
