@@ -333,10 +333,14 @@ __global__ void k_sum(const float *a, int n, float *out) {
 //                  back over the slot's tile, or after the last layer a
 //                  softmax staged in shared memory and stored coalesced.
 // Layer 1 (4 inputs) is one K = 16 MMA on split operands: with
-// x = x_hi + x_lo and W = W_hi + W_lo (BF16 parts), the A row holds
-// (x_hi, x_lo, x_hi, 0) and the B row (W_hi, W_hi, W_lo, 0), so the FP32
-// accumulator receives x_hi W_hi + x_lo W_hi + x_hi W_lo, the product up to
-// the x_lo W_lo term (relative ~2^-16).
+// x = x_hi + x_lo, W = W_hi + W_lo and b = b_hi + b_lo (BF16 parts), the A
+// row holds (x_hi, x_lo, x_hi, 1, 1, 0, 0) and the B row (W_hi, W_hi, W_lo,
+// b_hi, b_lo, 0, 0), so the FP32 accumulator receives
+// x_hi W_hi + x_lo W_hi + x_hi W_lo + b, the affine map up to the x_lo W_lo
+// term (relative ~2^-16).  The other layers add their bias the same way: a
+// first K = 16 MMA of a row of ones (one 8 x 16 block read with a zero
+// row-group stride) with (b_hi, b_lo, 0, ...) initialises the accumulator,
+// so the epilogue reads finished pre-activations from TMEM.
 // A warp may read only the TMEM lanes 32 (warp mod 4) .. +31, so epilogue
 // warp w serves rows 32 (w mod 4) + lane and one half of the columns.
 // Every wait is bounded; a wait that gives up sets the status flag and the
@@ -360,8 +364,8 @@ struct FusedArgs {
     float *P;
     int ncls;
     float4 shift, scale;
-    const bf16 *Wp[F_MAXL + 1];    // packed operand of every layer (layer 0: split K = 16)
-    const float *bh[F_MAXL + 1];   // biases
+    const bf16 *Wp[F_MAXL + 1];    // packed operand of every layer (layer 0: split K = 16 with bias)
+    const bf16 *Bp[F_MAXL + 1];    // packed bias operand (N x 16) of layers >= 1
     int nt;                        // layers; the last one is the output
     int p_aligned;                 // P 16-byte aligned: output tiles by bulk copy
     int *status;
@@ -386,7 +390,9 @@ __device__ __forceinline__ uint32_t pack_bf16(float lo, float hi) {
     return *reinterpret_cast<uint32_t *>(&v);
 }
 
-__device__ __forceinline__ int layer_chunks(int l) { return l == 0 ? 1 : 256 / FK; }
+// ring chunks of layer l: layer 0 one K = 16 chunk; the others a bias
+// chunk (N x 16) followed by the weight chunks
+__device__ __forceinline__ int layer_chunks(int l) { return l == 0 ? 1 : 1 + 256 / FK; }
 
 __global__ void __launch_bounds__(F_THREADS, 1) k_mlp_fused(FusedArgs a) {
     extern __shared__ __align__(1024) unsigned char sm[];
@@ -396,8 +402,15 @@ __global__ void __launch_bounds__(F_THREADS, 1) k_mlp_fused(FusedArgs a) {
     uint64_t *accf = empty + F_STAGES;     // per slot: accumulator complete
     uint64_t *actr = accf + 2;             // per slot: activations written, TMEM read
     uint32_t *s_tmem = reinterpret_cast<uint32_t *>(actr + 2);
+    unsigned char *ones = reinterpret_cast<unsigned char *>(s_tmem + 4);   // 8 x 16 BF16 block
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     if (warp == 1) umma::tmem_alloc(s_tmem, 512);
+    if (tid < 128) {
+        // BF16 element e of the block is (r, k) = ((e % 64) / 8, 8 (e / 64) + e % 8)
+        const int k = (tid >> 6) * 8 + (tid & 7);
+        reinterpret_cast<bf16 *>(ones)[tid] = __float2bfloat16_rn(k < 2 ? 1.f : 0.f);
+    }
+    umma::fence_proxy_smem();
     if (tid == 0) {
         for (int i = 0; i < F_STAGES; ++i) {
             umma::mbar_init(&full[i], 1);
@@ -429,9 +442,11 @@ __global__ void __launch_bounds__(F_THREADS, 1) k_mlp_fused(FusedArgs a) {
                 for (int l = 0; l < nt && !bad; ++l)
                     for (int s = 0; s < 2 && !bad; ++s) {
                         if (2 * p + s >= my_tiles) continue;
-                        const int N = l == nt - 1 ? 128 : 256, K = l == 0 ? 16 : FK;
-                        const uint32_t bytes = (uint32_t)(N * K * 2);
+                        const int N = l == nt - 1 ? 128 : 256;
                         for (int kc = 0; kc < layer_chunks(l); ++kc, ++c) {
+                            const bool small = l == 0 || kc == 0;     // K = 16 chunk
+                            const uint32_t bytes = (uint32_t)(N * (small ? 16 : FK) * 2);
+                            const bf16 *srcp = l == 0 ? a.Wp[0] : kc == 0 ? a.Bp[l] : a.Wp[l] + (size_t)(kc - 1) * N * FK;
                             // from the second pass on, wait until the MMAs of
                             // the previous pass have released the stage
                             if (c >= F_STAGES && !umma::mbar_wait(&empty[st], ph ^ 1u, GEMM_WAIT_NS)) {
@@ -439,8 +454,7 @@ __global__ void __launch_bounds__(F_THREADS, 1) k_mlp_fused(FusedArgs a) {
                                 break;
                             }
                             umma::mbar_expect_tx(&full[st], bytes);
-                            umma::bulk_g2s(ring + st * F_CHUNK_BYTES, a.Wp[l] + (size_t)kc * N * K, bytes,
-                                           &full[st]);
+                            umma::bulk_g2s(ring + st * F_CHUNK_BYTES, srcp, bytes, &full[st]);
                             if (++st == F_STAGES) {
                                 st = 0;
                                 ph ^= 1u;
@@ -469,6 +483,7 @@ __global__ void __launch_bounds__(F_THREADS, 1) k_mlp_fused(FusedArgs a) {
             uint32_t last_ph = 0;
             const uint64_t ring_desc = umma::desc(umma::saddr(ring), 128, F_SBO_B);
             const uint64_t ring_desc0 = umma::desc(umma::saddr(ring), 128, F_SBO_B0);
+            const uint64_t ones_desc = umma::desc(umma::saddr(ones), 128, 0);   // every row group: the same 8 rows
             uint32_t kpar[2] = {0u, 0u};   // per slot: parity of the next actr phase
             for (long long p = 0; p < npairs && !bad; ++p)
                 for (int l = 0; l < nt && !bad; ++l)
@@ -489,15 +504,17 @@ __global__ void __launch_bounds__(F_THREADS, 1) k_mlp_fused(FusedArgs a) {
                                 break;
                             }
                             umma::fence_after();
-                            const uint64_t bdesc = (l == 0 ? ring_desc0 : ring_desc) + (uint64_t)((st * F_CHUNK_BYTES) >> 4);
+                            const uint64_t soff = (uint64_t)((st * F_CHUNK_BYTES) >> 4);
                             if (l == 0) {
-                                umma::mma(d, act_desc, bdesc, idesc, 0u);
+                                umma::mma(d, act_desc, ring_desc0 + soff, idesc, 0u);
+                            } else if (kc == 0) {
+                                umma::mma(d, ones_desc, ring_desc0 + soff, idesc, 0u);     // accumulator = bias
                             } else {
-                                const uint64_t adesc = act_desc + (uint64_t)((kc * (FK / 8) * 128) >> 4);
+                                const uint64_t adesc = act_desc + (uint64_t)(((kc - 1) * (FK / 8) * 128) >> 4);
 #pragma unroll
                                 for (int k4 = 0; k4 < FK / 16; ++k4)
-                                    umma::mma(d, adesc + (uint64_t)(k4 * 16), bdesc + (uint64_t)(k4 * 16), idesc,
-                                              (kc | k4) ? 1u : 0u);
+                                    umma::mma(d, adesc + (uint64_t)(k4 * 16), ring_desc + soff + (uint64_t)(k4 * 16),
+                                              idesc, 1u);
                             }
                             umma::commit(&empty[st]);
                             last_st = st;
@@ -546,6 +563,7 @@ __global__ void __launch_bounds__(F_THREADS, 1) k_mlp_fused(FusedArgs a) {
                     u0.w = pack_bf16(f2 - g23.x, f3 - g23.y);
                     u1.x = u0.x;
                     u1.y = u0.y;
+                    u1.z = pack_bf16(1.f, 1.f);     // k = 12, 13: the bias columns
                 }
                 *reinterpret_cast<uint4 *>(act + act_off(r, 0)) = u0;
                 *reinterpret_cast<uint4 *>(act + act_off(r, 8)) = u1;
@@ -561,7 +579,6 @@ __global__ void __launch_bounds__(F_THREADS, 1) k_mlp_fused(FusedArgs a) {
                     break;
                 }
                 umma::fence_after();
-                const float *bias = a.bh[l];
                 if (l < nt - 1) {
                     // 8 groups of 16 columns; the TMEM load of group g + 1 is
                     // in flight while group g is computed
@@ -573,15 +590,11 @@ __global__ void __launch_bounds__(F_THREADS, 1) k_mlp_fused(FusedArgs a) {
                     for (int g = 0; g < 8; ++g) {
                         const int cur = g & 1, nxt = cur ^ 1;
                         if (g < 7) umma::ld16_async(trow + (uint32_t)(cb + 16 * (g + 1)), v[nxt]);
-                        float4 bq[4];
-#pragma unroll
-                        for (int i = 0; i < 4; ++i) bq[i] = __ldg(reinterpret_cast<const float4 *>(bias + cb + 16 * g) + i);
-                        const float *bb = reinterpret_cast<const float *>(bq);
                         uint32_t hv[8];
 #pragma unroll
                         for (int i = 0; i < 8; ++i)
-                            hv[i] = pack_bf16(silu_fast(__uint_as_float(v[cur][2 * i]) + bb[2 * i]),
-                                              silu_fast(__uint_as_float(v[cur][2 * i + 1]) + bb[2 * i + 1]));
+                            hv[i] = pack_bf16(silu_fast(__uint_as_float(v[cur][2 * i])),
+                                              silu_fast(__uint_as_float(v[cur][2 * i + 1])));
                         *reinterpret_cast<uint4 *>(act + act_off(r, cb + 16 * g)) = make_uint4(hv[0], hv[1], hv[2], hv[3]);
                         *reinterpret_cast<uint4 *>(act + act_off(r, cb + 16 * g + 8)) = make_uint4(hv[4], hv[5], hv[6], hv[7]);
                         if (g < 7) umma::wait_ld(v[nxt]);
@@ -599,14 +612,10 @@ __global__ void __launch_bounds__(F_THREADS, 1) k_mlp_fused(FusedArgs a) {
                     for (int c0 = cbeg; c0 < cend; c0 += 16) {
                         uint32_t v[16];
                         umma::ld16_async(trow + (uint32_t)c0, v);
-                        float4 b4[4];
-#pragma unroll
-                        for (int i = 0; i < 4; ++i) b4[i] = __ldg(reinterpret_cast<const float4 *>(bias + c0) + i);
-                        const float *bb = reinterpret_cast<const float *>(b4);
                         umma::wait_ld(v);
 #pragma unroll
                         for (int i = 0; i < 16; ++i)
-                            if (c0 + i < cend) mx = fmaxf(mx, __uint_as_float(v[i]) + bb[i]);
+                            if (c0 + i < cend) mx = fmaxf(mx, __uint_as_float(v[i]));
                     }
                     red[half * 128 + r] = mx;
                     umma::bar_sync(bar_id, nthr);
@@ -615,15 +624,11 @@ __global__ void __launch_bounds__(F_THREADS, 1) k_mlp_fused(FusedArgs a) {
                     for (int c0 = cbeg; c0 < cend; c0 += 16) {
                         uint32_t v[16];
                         umma::ld16_async(trow + (uint32_t)c0, v);
-                        float4 b4[4];
-#pragma unroll
-                        for (int i = 0; i < 4; ++i) b4[i] = __ldg(reinterpret_cast<const float4 *>(bias + c0) + i);
-                        const float *bb = reinterpret_cast<const float *>(b4);
                         umma::wait_ld(v);
 #pragma unroll
                         for (int i = 0; i < 16; ++i)
                             if (c0 + i < cend) {
-                                const float ez = __expf(__uint_as_float(v[i]) + bb[i] - mx);
+                                const float ez = __expf(__uint_as_float(v[i]) - mx);
                                 sum += ez;
                                 stage[r * ncls + c0 + i] = ez;
                             }
@@ -663,23 +668,35 @@ __global__ void __launch_bounds__(F_THREADS, 1) k_mlp_fused(FusedArgs a) {
     if (warp == 1) umma::tmem_free(tmem, 512);
 }
 
-constexpr size_t FUSED_SMEM = 2 * F_ACT_BYTES + F_STAGES * F_CHUNK_BYTES + (2 * F_STAGES + 4) * 8 + 16;
+constexpr size_t FUSED_SMEM = 2 * F_ACT_BYTES + F_STAGES * F_CHUNK_BYTES + (2 * F_STAGES + 4) * 8 + 16 + 256;
 static_assert(FUSED_SMEM <= 232448, "fused MLP shared memory above 227 KB");
 static_assert(128 * MLP_MAX_CLASSES * 4 <= F_RED_OFF && F_RED_OFF + 4 * 128 * 4 <= F_ACT_BYTES,
               "softmax stage overlaps the partials");
 
-// Packs layer 1, W [256][4] FP32, into the split K = 16 operand
-// (W_hi, W_hi, W_lo, 0) in the shared-memory layout.
-__global__ void k_pack0(const float *W, bf16 *out) {
+// Splits v into BF16 parts: part 0 = bf16(v), part 1 = bf16(v - part 0).
+__device__ __forceinline__ float split_part(float v, int part) {
+    const float hi = __bfloat162float(__float2bfloat16_rn(v));
+    return part == 0 ? hi : v - hi;
+}
+
+// Packs layer 1, W [256][4] and b [256] FP32, into the split K = 16 operand
+// (W_hi, W_hi, W_lo, b_hi, b_lo, 0, 0) in the shared-memory layout.
+__global__ void k_pack0(const float *W, const float *b, bf16 *out) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= 256 * 16) return;
     const int n = i / 16, k = i % 16;
     float v = 0.f;
-    if (k < 12) {
-        const float w = W[n * 4 + (k & 3)];
-        const float hi = __bfloat162float(__float2bfloat16_rn(w));
-        v = k < 8 ? hi : w - hi;
-    }
+    if (k < 12) v = split_part(W[n * 4 + (k & 3)], k < 8 ? 0 : 1);
+    else if (k < 14) v = split_part(b[n], k - 12);
+    out[(n >> 3) * (F_SBO_B0 / 2) + (k >> 3) * 64 + (n & 7) * 8 + (k & 7)] = __float2bfloat16_rn(v);
+}
+
+// Packs the bias b [N] into the K = 16 operand (b_hi, b_lo, 0, ...).
+__global__ void k_packb(const float *b, int N, bf16 *out) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= N * 16) return;
+    const int n = i / 16, k = i % 16;
+    const float v = k < 2 ? split_part(b[n], k) : 0.f;
     out[(n >> 3) * (F_SBO_B0 / 2) + (k >> 3) * 64 + (n & 7) * 8 + (k & 7)] = __float2bfloat16_rn(v);
 }
 
@@ -706,6 +723,7 @@ struct mlp_model {
     std::vector<float *> W, b, mW, vW, mb, vb, gW, gb;
     std::vector<bf16 *> Wh, Wt;   // BF16 [outp][in] and [in][outp] (layers >= 1)
     std::vector<bf16 *> Wp;       // chunk-packed copies for the fused forward pass
+    std::vector<bf16 *> Bp;       // packed bias operands (layers >= 1)
     bool packed = false;
     int adam_t = 0;
     // workspace
@@ -902,6 +920,7 @@ int mlp_create(int32_t n_hidden, int32_t width, int32_t n_classes, const float *
     m->Wh.assign(m->nl, nullptr);
     m->Wt.assign(m->nl, nullptr);
     m->Wp.assign(m->nl, nullptr);
+    m->Bp.assign(m->nl, nullptr);
     for (int l = 0; l < m->nl; ++l) {
         const size_t nw = (size_t)m->outp[l] * m->in[l], nbias = (size_t)m->outp[l];
         A((void **)&m->W[l], nw * 4);
@@ -916,6 +935,7 @@ int mlp_create(int32_t n_hidden, int32_t width, int32_t n_classes, const float *
             A((void **)&m->Wh[l], nw * 2);
             A((void **)&m->Wt[l], nw * 2);
             A((void **)&m->Wp[l], nw * 2);
+            A((void **)&m->Bp[l], (size_t)m->outp[l] * 16 * 2);
         } else {
             A((void **)&m->Wp[0], (size_t)m->outp[0] * 16 * 2);
         }
@@ -994,10 +1014,11 @@ int mlp_forward(mlp_model *m, const float *X, int64_t M, float *P_out, void *str
     if ((uintptr_t)X & 15) return fail(MD_E_ARG, "mlp_forward: X must be 16-byte aligned");
     cudaStream_t st = (cudaStream_t)stream;
     if (!m->packed) {
-        k_pack0<<<16, 256, 0, st>>>(m->W[0], m->Wp[0]);
+        k_pack0<<<16, 256, 0, st>>>(m->W[0], m->b[0], m->Wp[0]);
         for (int l = 1; l < m->nl; ++l) {
             const int n = m->outp[l] * 256;
             k_pack<<<(n + 255) / 256, 256, 0, st>>>(m->Wh[l], m->outp[l], m->Wp[l]);
+            k_packb<<<(m->outp[l] * 16 + 255) / 256, 256, 0, st>>>(m->b[l], m->outp[l], m->Bp[l]);
         }
         MD_CUDA_TRY(cudaGetLastError());
         m->packed = true;
@@ -1012,7 +1033,7 @@ int mlp_forward(mlp_model *m, const float *X, int64_t M, float *P_out, void *str
     a.nt = m->nl;
     for (int l = 0; l < m->nl; ++l) {
         a.Wp[l] = m->Wp[l];
-        a.bh[l] = m->b[l];
+        a.Bp[l] = m->Bp[l];
     }
     a.p_aligned = ((uintptr_t)P_out & 15) == 0;
     a.status = m->status;
