@@ -131,13 +131,6 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
-def _dist():
-    ws = int(os.environ.get("WORLD_SIZE", "1"))
-    rank = int(os.environ.get("RANK", "0"))
-    local = int(os.environ.get("LOCAL_RANK", "0"))
-    return ws, rank, local
-
-
 def ensemble(seed_offset=0, reps=None):
     """Per-replica parameters and initial states of the batched ensemble."""
     from paper_2101_01160_gb300 import inputs
@@ -241,9 +234,9 @@ def run_profile_case(args):
 def run_ours(args):
     import torch
 
-    from paper_2101_01160_gb300 import inputs, mdlg
+    from paper_2101_01160_gb300 import inputs, mdlg, sharding
 
-    ws, rank, local = _dist()
+    ws, rank, local = sharding.world()
     torch.cuda.set_device(local)
     dist = None
     if ws > 1:
@@ -252,7 +245,7 @@ def run_ours(args):
         dist_.init_process_group("nccl")
         dist = dist_
     mdlg.load()
-    ens = ensemble(seed_offset=rank)
+    ens = ensemble(seed_offset=sharding.seed_offset(rank))
     ntot = sum(e[0] for e in ens)
     cat = [np.concatenate([getattr(e[4], f) for e in ens]) for f in ("x", "y", "vx", "vy")]
     stream = torch.cuda.current_stream()
@@ -282,14 +275,10 @@ def run_ours(args):
     sysm.sync()
     step_ms = sum(a.elapsed_time(c) for a, b, c in ev)
     kern_ms = [a.elapsed_time(b) for a, b, c in ev]
-    t_max = step_ms
-    if dist:
-        t = torch.tensor([step_ms], device="cuda", dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        t_max = float(t.item())
-        dist.barrier()
+    # whole job: particle-steps summed over ranks / slowest rank's timed region
+    ps_all, t_max = sharding.aggregate(dist, ntot * MD_PER_STEP * args.steps, step_ms)
     ms_per_step = t_max / args.steps
-    value = ws * ntot * MD_PER_STEP / (ms_per_step * 1e-3)
+    value = ps_all / (t_max * 1e-3)
     stats = feq_dev[:, 3 * nb:].cpu().numpy()
     feq_err = {"max_abs_md_vs_wsg": float(stats[:, 6].max()),
                "max_abs_md_vs_gauss": float(stats[:, 4].max()),
@@ -309,8 +298,9 @@ def run_ours(args):
         sysm.step(MD_PER_STEP)
         mdlg.feq_batch(sysm, 0, 0, True)
     torch.cuda.synchronize()
-    e2e_s = (time.perf_counter() - t0) / e2e_steps
-    e2e = {"value": ws * ntot * MD_PER_STEP / e2e_s, "unit": UNIT,
+    e2e_ps, e2e_ms = sharding.aggregate(dist, ntot * MD_PER_STEP * e2e_steps,
+                                        (time.perf_counter() - t0) * 1e3)
+    e2e = {"value": e2e_ps / (e2e_ms * 1e-3), "unit": UNIT,
            "h2d_bytes_per_step": 4 * 8 * ntot,
            "d2h_bytes_per_step": N_REP * (3 * nb + mdlg.FEQB_STATS) * 8}
     info = sysm.info()
@@ -388,7 +378,9 @@ def cpu_baseline():
 
 
 def run_reference(args):
-    ws, rank, _ = _dist()
+    from paper_2101_01160_gb300 import sharding
+
+    ws, rank, _ = sharding.world()
     if rank != 0:
         return
     reps = [0, 128]
