@@ -438,6 +438,31 @@ int configure_launch(md_system *s, int block, int ppt, int stage) {
     const long long q = (nch + maxco - 1) / maxco;
     const long long grid = std::min<long long>(4096, std::max<long long>(1, (nch + q - 1) / q));
     if (q > MAX_CPC) return fail(MD_E_LIMIT, "more than %d chunks per CTA: raise per_thread", MAX_CPC);
+    // CTA b owns table entries b, b + grid, b + 2 grid, ...  Chunks differ in
+    // cost by the replicas' densities (neighbours per particle), so they are
+    // dealt by decreasing estimated cost, the CTA order reversed every other
+    // round, which evens out the per-CTA sums and the wait at the step's grid
+    // barrier.  Which CTA computes a chunk does not change any result.
+    {
+        std::vector<double> cost(nch);
+        for (long long k = 0; k < nch; ++k) {
+            const RepDev &R = s->reps[ch[k].x];
+            const double nbr = M_PI * R.rv2 * (double)R.n / (R.L * R.L);
+            cost[k] = (double)(ch[k].z - ch[k].y) * (6.0 + nbr);
+        }
+        std::vector<long long> order(nch);
+        for (long long k = 0; k < nch; ++k) order[k] = k;
+        std::stable_sort(order.begin(), order.end(),
+                         [&](long long a, long long b) { return cost[a] > cost[b]; });
+        std::vector<int4> dealt(nch);
+        for (long long k = 0; k < nch; ++k) {
+            const long long round = k / grid, w = k % grid;
+            const bool full = (round + 1) * grid <= nch;
+            const long long b = (full && (round & 1)) ? grid - 1 - w : w;
+            dealt[round * grid + b] = ch[order[k]];
+        }
+        ch.swap(dealt);
+    }
     MD_CUDA_TRY(cudaMemcpyAsync(s->d_chunks, ch.data(), sizeof(int4) * ch.size(),
                                 cudaMemcpyHostToDevice, s->st));
     s->smem = smem;

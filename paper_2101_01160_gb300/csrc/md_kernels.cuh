@@ -101,8 +101,10 @@ template <> struct WinParts<double> { static constexpr int value = 1536; };
 
 // neighbour-list entry: [31:30] dcy+1, [29:28] dcx+1, [27:0] slot
 constexpr uint32_t NB_INDEX = (1u << 28) - 1u;
-// list entries per particle staged in shared memory with the chunk
-constexpr int NB_STAGE = 8;
+// list entries per particle read in one batch (and staged in shared memory
+// with the chunk): 4 in FP32, 8 in FP64 (fewer register spills at each
+// precision's register budget; measured)
+template <typename T> constexpr int NB_STAGE = sizeof(T) == 4 ? 4 : 8;
 
 template <typename T> __device__ __forceinline__ T rd(double d, float f);
 template <> __device__ __forceinline__ double rd<double>(double d, float) { return d; }
@@ -298,11 +300,11 @@ __device__ __forceinline__ void stage_chunk(const SysDev &S, const RepDev &R, co
     for (int i = tid; i < len; i += BLOCK) cp_async_v(&B.vel[i], &vel[d.start + i]);
     for (int i = 4 * tid; i < len; i += 4 * BLOCK) cp_async16(&B.nn[i], &S.nn[d.start + i]);
     const int ngrp = (len + 31) >> 5;
-    const int per = NB_STAGE * 32 / 4;            // 16-byte pieces per group
+    const int per = NB_STAGE<T> * 32 / 4;            // 16-byte pieces per group
     for (int t = tid; t < ngrp * per; t += BLOCK) {
         const int g = t / per, r = t % per;
         const uint32_t *src = S.nbr + (long long)((d.start >> 5) + g) * S.K * 32 + r * 4;
-        cp_async16(&B.ent[g * NB_STAGE * 32 + r * 4], src);
+        cp_async16(&B.ent[g * NB_STAGE<T> * 32 + r * 4], src);
     }
 }
 
@@ -355,10 +357,10 @@ __device__ __forceinline__ int build_list(const SysDev &S, const RepDev &R,
 // are read from shared memory, the others (column-wrapped neighbours of
 // edge particles, chunks without a window) from global memory.
 template <typename T>
-__device__ __forceinline__ void lj_list(const SysDev &S, const RepDev &R, const ChunkDesc &d,
-                                        const typename V2<T>::type *spos, const uint32_t *sent,
-                                        const typename V2<T>::type *pin, typename V2<T>::type oi,
-                                        int self, int cnt, T &fx, T &fy) {
+__device__ __forceinline__ void lj_list_from(const SysDev &S, const RepDev &R, const ChunkDesc &d,
+                                             const typename V2<T>::type *spos,
+                                             const typename V2<T>::type *pin, typename V2<T>::type oi,
+                                             int self, int cnt, uint32_t (&e)[NB_STAGE<T>], T &fx, T &fy) {
     const T h = rd<T>(R.h, R.hf);
     const T rc2 = rd<T>(R.rc2, R.rc2f);
     const T eps24 = T(24) * rd<T>(R.eps, R.epsf);
@@ -367,15 +369,15 @@ __device__ __forceinline__ void lj_list(const SysDev &S, const RepDev &R, const 
     const T sys[3] = {-h - oi.y, -oi.y, h - oi.y};
     const uint32_t *lst = S.nbr + (long long)(self >> 5) * S.K * 32 + (self & 31);
     double pe_unused = 0.0, fa_unused = 0.0;
-    constexpr int U = NB_STAGE;
+    constexpr int U = NB_STAGE<T>;
+    // e holds the first batch; each later batch is requested while the
+    // previous one is computed.
     for (int k0 = 0; k0 < cnt; k0 += U) {
-        uint32_t e[U];
-        if (k0 == 0 && sent) {
+        uint32_t en[U];
+        const bool more = k0 + U < cnt;
+        if (more) {
 #pragma unroll
-            for (int u = 0; u < U; ++u) e[u] = u < cnt ? sent[u * 32] : 0u;
-        } else {
-#pragma unroll
-            for (int u = 0; u < U; ++u) e[u] = k0 + u < cnt ? lst[(k0 + u) * 32] : 0u;
+            for (int u = 0; u < U; ++u) en[u] = k0 + U + u < cnt ? lst[(k0 + U + u) * 32] : 0u;
         }
 #pragma unroll
         for (int u = 0; u < U; ++u) {
@@ -391,7 +393,26 @@ __device__ __forceinline__ void lj_list(const SysDev &S, const RepDev &R, const 
                                       fa_unused);
             }
         }
+        if (more) {
+#pragma unroll
+            for (int u = 0; u < U; ++u) e[u] = en[u];
+        }
     }
+}
+
+// lj_list_from with the first batch of list entries read here: without
+// waiting for the count (a list holds K >= NB_STAGE entries, so the reads
+// stay in bounds; unused ones are masked), from shared memory if staged.
+template <typename T>
+__device__ __forceinline__ void lj_list(const SysDev &S, const RepDev &R, const ChunkDesc &d,
+                                        const typename V2<T>::type *spos, const uint32_t *sent,
+                                        const typename V2<T>::type *pin, typename V2<T>::type oi,
+                                        int self, int cnt, T &fx, T &fy) {
+    uint32_t e[NB_STAGE<T>];
+    const uint32_t *lst = S.nbr + (long long)(self >> 5) * S.K * 32 + (self & 31);
+#pragma unroll
+    for (int u = 0; u < NB_STAGE<T>; ++u) e[u] = sent ? sent[u * 32] : lst[u * 32];
+    lj_list_from<T>(S, R, d, spos, pin, oi, self, cnt, e, fx, fy);
 }
 
 // ---------------------------------------------------------------- rebuild
@@ -649,7 +670,7 @@ __host__ __device__ inline size_t stage_bytes(int chunk) {
     using V = typename V2<T>::type;
     return align16((size_t)WinParts<T>::value * sizeof(V)) + align16((size_t)chunk * sizeof(V)) +
            align16((size_t)(chunk + 4) * sizeof(int32_t)) +
-           align16((size_t)chunk * NB_STAGE * sizeof(uint32_t));
+           align16((size_t)chunk * NB_STAGE<T> * sizeof(uint32_t));
 }
 template <typename T>
 __device__ inline Stage<T> stage_at(unsigned char *p, int chunk) {
@@ -788,7 +809,7 @@ __global__ void __launch_bounds__(BLOCK, BLOCK == 256 ? 4 : 8) k_md_persistent(S
                     const int ks = d.ok ? window_index(d, R, slot) : -1;
                     const V oi = ks >= 0 ? B.pos[ks] : pin[slot];
                     T fx = T(0), fy = T(0);
-                    lj_list<T>(S, R, d, B.pos, B.ent + (li >> 5) * NB_STAGE * 32 + (li & 31), pin,
+                    lj_list<T>(S, R, d, B.pos, B.ent + (li >> 5) * NB_STAGE<T> * 32 + (li & 31), pin,
                                oi, slot, B.nn[li], fx, fy);
                     kick_drift<T>(R, oi, B.vel[li], fx, fy, hk, dt, first, vscale, pout, vel, slot, vm,
                                   bad);
@@ -806,10 +827,10 @@ __global__ void __launch_bounds__(BLOCK, BLOCK == 256 ? 4 : 8) k_md_persistent(S
                 const float vscale = (float)(R.dt / R.half_skin);
                 for (int slot = cd.y + tid; slot < cd.z; slot += BLOCK) {
                     const V oi = pin[slot];
+                    const V vi = vel[slot];   // requested now, used after the force sum
                     T fx = T(0), fy = T(0);
                     lj_list<T>(S, R, none, nullptr, nullptr, pin, oi, slot, S.nn[slot], fx, fy);
-                    kick_drift<T>(R, oi, vel[slot], fx, fy, hk, dt, first, vscale, pout, vel, slot,
-                                  vm, bad);
+                    kick_drift<T>(R, oi, vi, fx, fy, hk, dt, first, vscale, pout, vel, slot, vm, bad);
                 }
             }
         }
