@@ -273,11 +273,16 @@ int feq_batch(md_system *s, int32_t lg, int32_t dxi, int32_t symmetrize, double 
 int mdlg_bin(const md_snapshot *t0, const md_snapshot *t1, int64_t n, int32_t lx, int32_t W,
              int32_t *hist_out, int64_t *overflow_out, double *mom_out, void *stream);
 
-/* mdlg_bin without any device allocation (the paper has no counterpart:
- * this is a library convenience for callers that must not allocate, e.g.
- * inside a memory-pool-free loop).  Same arguments, same results bit for
- * bit (same launch shape).  The per-CTA moment partials go to one fixed
- * 32 KiB device array inside the library, room for 2048 CTAs; the grid is
+/* mdlg_bin without any device allocation.  The paper has no counterpart;
+ * this is for callers that cannot allocate device memory while they run:
+ * a process whose device memory is all handed to a framework's caching
+ * allocator or to a fixed budget at start-up (a cudaMalloc there fails or
+ * forces a device-wide synchronisation), or an analysis loop binning many
+ * snapshot pairs that must not stall on allocator calls.  Same arguments,
+ * same results bit for bit (same launch shape).  The per-CTA moment
+ * partials go to one fixed 32 KiB device array inside the library (every
+ * GPU that loads the library holds it until the process exits), room for
+ * 2048 CTAs; the grid is
  * min(ceil(n/256), 8 x SM count), 1216 CTAs on a 152-SM GPU, and a call
  * that would need more returns MD_E_LIMIT.  The outputs are cleared with
  * cudaMemsetAsync on `stream`; the array needs no clearing.  The array is

@@ -130,10 +130,16 @@ int bin_launch(const md_snapshot *t0, const md_snapshot *t1, int64_t n, int32_t 
     return MD_OK;
 }
 
-// Moment partials of mdlg_bin_noalloc: a fixed device array instead of a
-// per-call allocation (2 doubles per CTA, room for BIN_SCRATCH_CTAS CTAs,
-// 32 KiB).  Every CTA of a launch overwrites its own two entries and the
-// reduction reads only the first `grid`, so it never needs clearing.
+// Moment partials of mdlg_bin_noalloc, for callers that cannot allocate
+// device memory while they run (their memory belongs to a framework's
+// caching allocator or a fixed budget, or their loop must not stall on
+// allocator calls): a fixed device array instead of a per-call allocation
+// (2 doubles per CTA, room for BIN_SCRATCH_CTAS CTAs, 32 KiB, held by every
+// GPU that loads the library until the process exits).  Every CTA of a
+// launch overwrites its own two entries and the reduction reads only the
+// first `grid`, so it never needs clearing.  Host code must not pass the
+// array's name to a kernel (on the host it only stands in for the symbol);
+// it passes the device address that cudaGetSymbolAddress returns.
 constexpr int BIN_SCRATCH_CTAS = 2048;
 static __device__ __align__(256) double g_bin_scratch[2 * BIN_SCRATCH_CTAS];
 
@@ -176,7 +182,10 @@ extern "C" int mdlg_bin(const md_snapshot *t0, const md_snapshot *t1, int64_t n,
 }
 
 // Same computation as mdlg_bin with the partials in g_bin_scratch.  The
-// array's device address is looked up once per device; nothing is allocated.
+// array's device address is looked up on the first call on each device
+// (with that device current), so that first call should come before any
+// stream capture; nothing is allocated.  Calls that overlap on the GPU share
+// the array and race.
 extern "C" int mdlg_bin_noalloc(const md_snapshot *t0, const md_snapshot *t1, int64_t n, int32_t lx,
                                 int32_t W, int32_t *hist_out, int64_t *overflow_out, double *mom_out,
                                 void *stream) {

@@ -1,7 +1,10 @@
-"""mdlg_bin_noalloc (library-owned scratch, no device allocation) against
-mdlg_bin on the same inputs, two calls in a row with different sizes so that
-stale partials of the first call would show in the second.  Named to be
-collected last; it also passes on its own."""
+"""mdlg_bin_noalloc, the binning entry point for callers that cannot
+allocate device memory while they run (memory owned by a framework's caching
+allocator or a fixed budget, or a loop that must not stall on allocator
+calls), against mdlg_bin on the same inputs: two calls in a row with
+different sizes, so that partials left in the shared scratch array by the
+first call would show in the second.  Named to be collected last; it also
+passes on its own."""
 
 import numpy as np
 import pytest
