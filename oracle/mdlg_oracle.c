@@ -27,6 +27,14 @@
  *   or_wsg_lambda                the roots lambda_{1,2} of Eq. (lambda_eq)
  *   or_wsg_mu4                   Eq. (fourth_order)
  *   or_kl                        Eq. (kullback_leibler) / Eq. (k_Xi)
+ *   or_disp_hist                 histogram of the continuous one-dimensional
+ *                                displacement component over bins X_i (the
+ *                                measured PDF of Sec. 3(b), Fig. 2)
+ *   or_pdf_gauss_bins            bin masses of the Gaussian displacement PDF,
+ *                                Eq. (gaussian_df), d = 1, u = 0
+ *   or_pdf_wsg_bins              bin masses of the Poisson WSG displacement
+ *                                PDF, Eqs. (poisson_v2) and (p_wsg_one)
+ *   or_kl_terms                  element-wise K(X_i) of Eq. (k_Xi)
  *   or_symmetrize                the symmetric-set averaging of Sec. 5
  *   or_forces_brute              the Lennard-Jones force of Sec. 4, all
  *                                pairs, minimum image, cutoff rc, potential
@@ -144,6 +152,73 @@ int or_bin_celloff(int64_t n, const int32_t *c0, const void *ox0, const void *oy
     return 0;
 }
 
+/* Histogram of the continuous one-dimensional displacement component: for
+ * every particle and both axes, delta = nearest image of x1 - x0 (the same
+ * quantity whose powers mom[] of or_bin_xy sums) falls in bin
+ * floor(delta / width) + nbins / 2 of nbins bins of the given width, bin k
+ * covering [(k - nbins/2) width, (k - nbins/2 + 1) width); a value on a bin
+ * edge goes to the upper bin.  Values outside all bins count in *outside,
+ * so sum(hist) + *outside = 2n.  Snapshots in the (cell, offset) encoding as
+ * for or_bin_celloff.  Accumulates. */
+int or_disp_hist(int64_t n, const int32_t *c0, const void *ox0, const void *oy0,
+                 const int32_t *c1, const void *ox1, const void *oy1, int32_t f64,
+                 int32_t ncell, double h, double L, double width, int32_t nbins,
+                 int64_t *hist, int64_t *outside)
+{
+    double *b = (double *)malloc(sizeof(double) * 4 * (size_t)(n > 0 ? n : 1));
+    if (!b) return -1;
+    decode(n, c0, ox0, oy0, f64, ncell, h, b, b + n);
+    decode(n, c1, ox1, oy1, f64, ncell, h, b + 2 * n, b + 3 * n);
+    for (int64_t j = 0; j < n; ++j) {
+        for (int axis = 0; axis < 2; ++axis) {
+            double d = nearest_image(b[(2 + axis) * n + j] - b[axis * n + j], L);
+            double k = floor(d / width) + (double)(nbins / 2);
+            if (k >= 0.0 && k < (double)nbins)
+                hist[(int64_t)k] += 1;
+            else
+                *outside += 1;
+        }
+    }
+    free(b);
+    return 0;
+}
+
+int32_t or_wsg_cmax(double lambda);
+double or_poisson(int32_t c, double lambda);
+
+/* Mass of a centred normal distribution of variance var in [a, b). */
+static double normal_mass(double a, double b, double var)
+{
+    double s = sqrt(2.0 * var);
+    return 0.5 * (erf(b / s) - erf(a / s));
+}
+
+/* Eq. (gaussian_df) with d = 1, u = 0 and <dx^2> = mu2, integrated over the
+ * bins of or_disp_hist. */
+void or_pdf_gauss_bins(double mu2, double width, int32_t nbins, double *P)
+{
+    for (int32_t k = 0; k < nbins; ++k) {
+        double a = (double)(k - nbins / 2) * width;
+        P[k] = normal_mass(a, a + width, mu2);
+    }
+}
+
+/* Eq. (poisson_v2) with the one-dimensional Gaussians of Eq. (p_wsg_one)
+ * (d = 1, u = 0): Poisson weights of the number c of collisions times a
+ * Gaussian of variance (c + 1) mu2 / (lambda + 1), integrated over the bins
+ * of or_disp_hist; c = 0 .. or_wsg_cmax(lambda). */
+void or_pdf_wsg_bins(double mu2, double lambda, double width, int32_t nbins, double *P)
+{
+    int32_t cmax = or_wsg_cmax(lambda);
+    for (int32_t k = 0; k < nbins; ++k) {
+        double a = (double)(k - nbins / 2) * width;
+        double s = 0.0;
+        for (int32_t c = 0; c <= cmax; ++c)
+            s += or_poisson(c, lambda) * normal_mass(a, a + width, (double)(c + 1) * mu2 / (lambda + 1.0));
+        P[k] = s;
+    }
+}
+
 /* ------------------------------------------------------------------------ */
 /* Eq. (feq_gaussian): one-dimensional Gaussian equilibrium for the shifted
  * lattice velocity u = v_i - u_alpha (lattice units) and a^2 = <dx^2>/dx^2,
@@ -249,6 +324,12 @@ int or_wsg_lambda(double mu2, double mu4, double *l1, double *l2)
     *l1 = (-9.0 * m22 + r + 2.0 * mu4) / den;
     *l2 = (-9.0 * m22 - r + 2.0 * mu4) / den;
     return 0;
+}
+
+/* Eq. (k_Xi): K(X_i) = R_i log(R_i / Q_i) per bin, 0 where R_i = 0. */
+void or_kl_terms(const double *R, const double *Q, int64_t n, double *K)
+{
+    for (int64_t i = 0; i < n; ++i) K[i] = R[i] > 0.0 ? R[i] * log(R[i] / Q[i]) : 0.0;
 }
 
 /* Eq. (kullback_leibler), with the convention 0 log 0 = 0. */

@@ -75,6 +75,14 @@ def _declare(L):
     L.or_wsg_lambda.restype = C.c_int
     L.or_kl.argtypes = [P, P, I64]
     L.or_kl.restype = D
+    L.or_kl_terms.argtypes = [P, P, I64, P]
+    L.or_kl_terms.restype = None
+    L.or_disp_hist.argtypes = [I64, P, P, P, P, P, P, I32, I32, D, D, D, I32, P, P]
+    L.or_disp_hist.restype = C.c_int
+    L.or_pdf_gauss_bins.argtypes = [D, D, I32, P]
+    L.or_pdf_gauss_bins.restype = None
+    L.or_pdf_wsg_bins.argtypes = [D, D, D, I32, P]
+    L.or_pdf_wsg_bins.restype = None
     L.or_symmetrize.argtypes = [P, I32, P]
     L.or_symmetrize.restype = None
     L.or_lj_pair.argtypes = [D, D, D, D, P]
@@ -126,6 +134,41 @@ def bin_celloff(s, ncell, h, L, lx, W):
                               _p(hist), _p(ovf), _p(mom))
     assert rc == 0
     return hist, int(ovf[0]), mom
+
+
+def disp_hist(s, ncell, h, L, width, nbins):
+    """Histogram of the continuous per-axis displacement (both axes) of the
+    snapshot pair s over nbins bins of the given width centred on 0; returns
+    (hist int64[nbins], outside)."""
+    f64 = s["ox0"].dtype == np.float64
+    ft = np.float64 if f64 else np.float32
+    arrs = [np.ascontiguousarray(s[k], dtype=(np.int32 if k.startswith("cell") else ft))
+            for k in ("cell0", "ox0", "oy0", "cell1", "ox1", "oy1")]
+    hist = np.zeros(nbins, np.int64)
+    out = np.zeros(1, np.int64)
+    rc = lib().or_disp_hist(len(arrs[0]), *[_p(a) for a in arrs], int(f64), ncell, h, L, width,
+                            nbins, _p(hist), _p(out))
+    assert rc == 0
+    return hist, int(out[0])
+
+
+def pdf_gauss_bins(mu2, width, nbins):
+    P_ = np.zeros(nbins)
+    lib().or_pdf_gauss_bins(float(mu2), float(width), int(nbins), _p(P_))
+    return P_
+
+
+def pdf_wsg_bins(mu2, lam, width, nbins):
+    P_ = np.zeros(nbins)
+    lib().or_pdf_wsg_bins(float(mu2), float(lam), float(width), int(nbins), _p(P_))
+    return P_
+
+
+def kl_terms(R, Q):
+    R, Q = _f64(R), _f64(Q)
+    K = np.zeros(len(R))
+    lib().or_kl_terms(_p(R), _p(Q), len(R), _p(K))
+    return K
 
 
 # ---------------------------------------------------------------- closed forms
