@@ -202,12 +202,42 @@ def _time_surrogate(mdlg, torch, n=1 << 20, reps=5):
             "kernel": "k_mlp_fused", "workload": "1,048,576 queries uniform in the training box"}
 
 
+def _time_disp_hist(mdlg, torch, n=1 << 24, reps=5):
+    """Displacement-PDF histogram (Sec. 3(b), Fig. 2) of a synthetic FP32
+    snapshot pair of n particles (400 MB, above L2); algorithmic traffic
+    24 B per particle (two snapshots of cell + two FP32 offsets)."""
+    from paper_2101_01160_gb300 import inputs
+
+    ncell = 2160
+    h = float(np.float32(6482.12 / ncell))
+    s = inputs.random_celloff_snapshots(n, ncell, h, seed=5, max_step=6.0)
+    arrs = [torch.from_numpy(s[k]).cuda() for k in ("cell0", "ox0", "oy0", "cell1", "ox1", "oy1")]
+    for _ in range(3):
+        mdlg.disp_hist(*arrs, ncell, h, 0.05, 512)
+    torch.cuda.synchronize()
+    ms = []
+    for _ in range(reps):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        mdlg.disp_hist(*arrs, ncell, h, 0.05, 512)
+        e1.record()
+        torch.cuda.synchronize()
+        ms.append(e0.elapsed_time(e1))
+    m = float(np.median(ms))
+    peak, kind = _peaks()
+    gbs = 24.0 * n / (m * 1e-3) / 1e9
+    return {"particles": n, "ms_per_launch": m, "gbs": gbs, "peak_gbs": peak, "peak_kind": kind,
+            "frac": gbs / peak, "kernel": "k_disp_hist", "bytes_per_particle": 24,
+            "workload": "synthetic FP32 snapshot pair, 16.8M particles, 512 bins of 0.05 sigma"}
+
+
 def run_profile_case(args):
     """Small cases for ncu captures (not a bench line): md64 = the first 64
     replicas of the batched ensemble (about 1.5M particles, > L2), fixed
     launch shape (256 threads, 1 chunk per thread, global staging), two
     400-step warm-up launches then three 100-step launches; mlp = three fused
-    surrogate forward passes on 1M queries."""
+    surrogate forward passes on 1M queries; disp = eight displacement-PDF
+    histograms of a 16.8M-particle snapshot pair."""
     import torch
 
     from paper_2101_01160_gb300 import mdlg
@@ -226,6 +256,9 @@ def run_profile_case(args):
         print(json.dumps({"profile_case": "md64", "n_particles": int(sum(e[0] for e in ens)),
                           "rebuilds": int(s.info().n_rebuilds)}))
         s.close()
+    elif args.profile_case == "disp":
+        r = _time_disp_hist(mdlg, torch, reps=3)
+        print(json.dumps({"profile_case": "disp", **r}))
     else:
         r = _time_surrogate(mdlg, torch, reps=3)
         print(json.dumps({"profile_case": "mlp", **r}))
@@ -319,6 +352,7 @@ def run_ours(args):
                                           "{0.5,1,2}, one 2000-step launch")
         variants["batched_fp32_over_plain_fp64"] = (value / ws) / variants["plain_fp64"]["value"]
         variants["surrogate_inference"] = _time_surrogate(mdlg, torch)
+        variants["disp_hist"] = _time_disp_hist(mdlg, torch)
 
     peak, peak_kind = _peaks()
     kern_avg_s = (sum(kern_ms) / len(kern_ms)) * 1e-3
@@ -414,7 +448,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-variants", action="store_true")
-    ap.add_argument("--profile-case", choices=["md64", "mlp"], default=None,
+    ap.add_argument("--profile-case", choices=["md64", "mlp", "disp"], default=None,
                     help="run a small case for ncu captures instead of the bench")
     args = ap.parse_args()
     if args.profile_case:

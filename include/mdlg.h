@@ -294,6 +294,38 @@ int mdlg_bin(const md_snapshot *t0, const md_snapshot *t1, int64_t n, int32_t lx
 int mdlg_bin_noalloc(const md_snapshot *t0, const md_snapshot *t1, int64_t n, int32_t lx, int32_t W,
                      int32_t *hist_out, int64_t *overflow_out, double *mom_out, void *stream);
 
+/* ---- displacement-PDF diagnostics (Sec. 3(b), Fig. 2) -------------------- */
+
+/* Histogram of the continuous one-dimensional displacement component between
+ * snapshots t0 and t1 (same ncell and h): for every particle and both axes,
+ * delta = wrap(c1 - c0) * h + (off1 - off0), the cell-index difference
+ * wrapped to the nearest periodic image (into [-ncell/2, ncell/2]) -- the
+ * continuous nearest-image displacement, evaluated in the cell frame with a
+ * single rounding -- falls in bin floor(delta * (1/width)) + nbins/2 (each
+ * operation rounded on its own; bin k covers about
+ * [(k - nbins/2) width, (k - nbins/2 + 1) width)).  Values outside all bins
+ * count in *outside_out, so sum(hist) + outside = 2n.  hist_out
+ * (int64[nbins]) and outside_out are device memory, overwritten; exact
+ * integers.  n < 2^31, 1 <= nbins <= 8192, width > 0, else MD_E_ARG.
+ * Asynchronous on stream. */
+int mdlg_disp_hist(const md_snapshot *t0, const md_snapshot *t1, int64_t n, double width,
+                   int32_t nbins, int64_t *hist_out, int64_t *outside_out, void *stream);
+
+/* Bin masses, over the bins of mdlg_disp_hist, of the one-dimensional
+ * Gaussian displacement PDF of second moment mu2 (Eq. gaussian_df, d = 1,
+ * u = 0) into pg_out, and of the Poisson weighted sum of Gaussians
+ * (Eq. poisson_v2 with the Gaussians of Eq. p_wsg_one, variance
+ * (c+1) mu2/(lambda+1), c over the window lambda +- (12 sqrt(lambda) + 20))
+ * into pwsg_out.  Device outputs (double[nbins]).  mu2 > 0,
+ * 0 <= lambda <= 1e5, width > 0, 1 <= nbins <= 8192, else MD_E_ARG. */
+int disp_pdf_models(double mu2, double lambda, double width, int32_t nbins, double *pg_out,
+                    double *pwsg_out, void *stream);
+
+/* Element-wise Kullback-Leibler terms of Eq. k_Xi, K_out[i] =
+ * R[i] log(R[i]/Q[i]) (0 where R[i] = 0); their sum is D_KL of
+ * Eq. kullback_leibler.  R, Q, K_out: device double[n]. */
+int kl_terms(const double *R, const double *Q, int32_t n, double *K_out, void *stream);
+
 /* ---- analytic equilibria (Sec. 3) ---------------------------------------- */
 
 /* Single-Gaussian equilibrium, Eqs. (feq_prod), (feq_gaussian): P_out[i] =

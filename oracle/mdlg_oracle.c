@@ -152,34 +152,42 @@ int or_bin_celloff(int64_t n, const int32_t *c0, const void *ox0, const void *oy
     return 0;
 }
 
-/* Histogram of the continuous one-dimensional displacement component: for
- * every particle and both axes, delta = nearest image of x1 - x0 (the same
- * quantity whose powers mom[] of or_bin_xy sums) falls in bin
- * floor(delta / width) + nbins / 2 of nbins bins of the given width, bin k
- * covering [(k - nbins/2) width, (k - nbins/2 + 1) width); a value on a bin
- * edge goes to the upper bin.  Values outside all bins count in *outside,
- * so sum(hist) + *outside = 2n.  Snapshots in the (cell, offset) encoding as
- * for or_bin_celloff.  Accumulates. */
+/* Histogram of the continuous one-dimensional displacement component over
+ * bins X_i.  For every particle and both axes the displacement is taken in
+ * the cell frame: the cell-index difference wrapped to the nearest periodic
+ * image (into [-ncell/2, ncell/2]) times h, plus the offset difference,
+ *     delta = wrap(c1 - c0) * h + (off1 - off0),
+ * which has a single rounding (none in the product and the offset
+ * difference when the offsets are FP32), instead of decoding two absolute
+ * positions near the box size.  Its bin is floor(delta * (1 / width)) +
+ * nbins / 2, with 1 / width rounded once; bin k covers roughly
+ * [(k - nbins/2) width, (k - nbins/2 + 1) width).  Values outside all bins
+ * count in *outside, so sum(hist) + *outside = 2n.  Accumulates. */
 int or_disp_hist(int64_t n, const int32_t *c0, const void *ox0, const void *oy0,
                  const int32_t *c1, const void *ox1, const void *oy1, int32_t f64,
                  int32_t ncell, double h, double L, double width, int32_t nbins,
                  int64_t *hist, int64_t *outside)
 {
-    double *b = (double *)malloc(sizeof(double) * 4 * (size_t)(n > 0 ? n : 1));
-    if (!b) return -1;
-    decode(n, c0, ox0, oy0, f64, ncell, h, b, b + n);
-    decode(n, c1, ox1, oy1, f64, ncell, h, b + 2 * n, b + 3 * n);
+    (void)L;
+    double inv_w = 1.0 / width;
     for (int64_t j = 0; j < n; ++j) {
+        int32_t cell0[2] = {c0[j] % ncell, c0[j] / ncell};
+        int32_t cell1[2] = {c1[j] % ncell, c1[j] / ncell};
+        const void *o0[2] = {ox0, oy0}, *o1[2] = {ox1, oy1};
         for (int axis = 0; axis < 2; ++axis) {
-            double d = nearest_image(b[(2 + axis) * n + j] - b[axis * n + j], L);
-            double k = floor(d / width) + (double)(nbins / 2);
+            int32_t dc = cell1[axis] - cell0[axis];
+            if (dc > ncell / 2) dc -= ncell;
+            if (dc < -(ncell / 2)) dc += ncell;
+            double a = f64 ? ((const double *)o0[axis])[j] : (double)((const float *)o0[axis])[j];
+            double b = f64 ? ((const double *)o1[axis])[j] : (double)((const float *)o1[axis])[j];
+            double d = (double)dc * h + (b - a);
+            double k = floor(d * inv_w) + (double)(nbins / 2);
             if (k >= 0.0 && k < (double)nbins)
                 hist[(int64_t)k] += 1;
             else
                 *outside += 1;
         }
     }
-    free(b);
     return 0;
 }
 

@@ -1,0 +1,163 @@
+// Displacement-PDF diagnostics (Sec. 3(b), Fig. 2): the histogram of the
+// continuous one-dimensional displacement component between two snapshots
+// over bins X_i, the bin masses of the Gaussian (Eq. gaussian_df) and
+// Poisson WSG (Eqs. poisson_v2, p_wsg_one) displacement PDFs, and the
+// element-wise K(X_i) of Eq. k_Xi.
+//
+// The displacement is taken in the cell frame, wrap(c1 - c0) * h +
+// (off1 - off0) with the cell difference wrapped to the nearest image: one
+// rounding (none but the final sum for FP32 offsets) and a handful of FP64
+// operations, the limiting resource of this kernel on GB300 (its FP64 pipe
+// runs near saturation).  The bin is floor(delta * (1 / width)), every
+// operation rounded on its own, so bin indices are exact.  The histogram is privatised per CTA in shared memory
+// and flushed with 64-bit atomics: integer counts do not depend on the
+// launch.
+#include <cmath>
+
+#include "common.cuh"
+#include "equilibria.cuh"
+#include "lattice.cuh"
+
+namespace mdlg {
+
+constexpr int PDF_MAX_BINS = 8192;    // 32 KB of shared counters per CTA
+
+struct PdfSnap {
+    const int32_t *cell;
+    const void *ox, *oy;
+    int f64;
+};
+
+template <typename T>
+__global__ void k_disp_hist(PdfSnap a, PdfSnap b, int n, int ncell, double h, double inv_w, int nbins,
+                            unsigned long long *hist, unsigned long long *outside) {
+    extern __shared__ unsigned int sh_bins[];
+    for (int k = threadIdx.x; k < nbins; k += blockDim.x) sh_bins[k] = 0u;
+    __syncthreads();
+    unsigned my_out = 0;
+    const long long lo = -(long long)(nbins / 2), hi = (long long)nbins - nbins / 2;
+    const T *o0[2] = {static_cast<const T *>(a.ox), static_cast<const T *>(a.oy)};
+    const T *o1[2] = {static_cast<const T *>(b.ox), static_cast<const T *>(b.oy)};
+    for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < n; j += gridDim.x * blockDim.x) {
+        const int c0 = a.cell[j], c1 = b.cell[j];
+        const int cc0[2] = {c0 % ncell, c0 / ncell}, cc1[2] = {c1 % ncell, c1 / ncell};
+#pragma unroll
+        for (int ax = 0; ax < 2; ++ax) {
+            int dc = cc1[ax] - cc0[ax];
+            if (dc > ncell / 2) dc -= ncell;
+            if (dc < -(ncell / 2)) dc += ncell;
+            const double doff = __dsub_rn((double)o1[ax][j], (double)o0[ax][j]);
+            const double d = __dadd_rn(__dmul_rn((double)dc, h), doff);
+            // floor(d / width) as an integer in one conversion (round down;
+            // the range test is then integer, no FP64 floor or compare)
+            const long long k = __double2ll_rd(__dmul_rn(d, inv_w));
+            if (k >= lo && k < hi)
+                atomicAdd(&sh_bins[(int)(k - lo)], 1u);
+            else
+                ++my_out;
+        }
+    }
+    for (int o = 16; o > 0; o >>= 1) my_out += __shfl_xor_sync(0xffffffffu, my_out, o);
+    if ((threadIdx.x & 31) == 0 && my_out) atomicAdd(outside, (unsigned long long)my_out);
+    __syncthreads();
+    for (int k = threadIdx.x; k < nbins; k += blockDim.x)
+        if (sh_bins[k]) atomicAdd(&hist[k], (unsigned long long)sh_bins[k]);
+}
+
+// Mass of a centred normal distribution of variance var in [lo, hi).
+__device__ __forceinline__ double normal_mass(double lo, double hi, double var) {
+    const double s = sqrt(__dmul_rn(2.0, var));
+    return 0.5 * (erf(hi / s) - erf(lo / s));
+}
+
+// One thread per bin: Gaussian of variance mu2 and the Poisson mixture of
+// Gaussians of variance (c + 1) mu2 / (lambda + 1) over the window of c.
+__global__ void k_pdf_models(double mu2, double lam, double width, int nbins, double *pg, double *pwsg) {
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= nbins) return;
+    const double lo = __dmul_rn((double)(k - nbins / 2), width);
+    const double hi = __dadd_rn(lo, width);
+    pg[k] = normal_mass(lo, hi, mu2);
+    double s = 0.0;
+    const int c1 = wsg_cmax(lam);
+    for (int c = wsg_cmin(lam); c <= c1; ++c)
+        s += poisson_weight(c, lam) * normal_mass(lo, hi, (double)(c + 1) * mu2 / (lam + 1.0));
+    pwsg[k] = s;
+}
+
+__global__ void k_kl_terms(const double *R, const double *Q, int n, double *K) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) K[i] = R[i] > 0.0 ? R[i] * log(R[i] / Q[i]) : 0.0;
+}
+
+int pdf_grid(int64_t n) {
+    static int nsm = 0;
+    if (nsm == 0) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+        if (nsm <= 0) nsm = 1;
+    }
+    int64_t g = (n + 255) / 256;
+    if (g > (int64_t)nsm * 8) g = (int64_t)nsm * 8;
+    return (int)(g < 1 ? 1 : g);
+}
+
+}  // namespace mdlg
+
+using namespace mdlg;
+
+extern "C" int mdlg_disp_hist(const md_snapshot *t0, const md_snapshot *t1, int64_t n, double width,
+                              int32_t nbins, int64_t *hist_out, int64_t *outside_out, void *stream) {
+    if (!t0 || !t1 || !hist_out || !outside_out) return fail(MD_E_ARG, "mdlg_disp_hist: NULL argument");
+    if (n < 0 || n >= (int64_t)1 << 31) return fail(MD_E_ARG, "mdlg_disp_hist: n out of [0, 2^31)");
+    if (n > 0 && (!t0->cell || !t0->off_x || !t0->off_y || !t1->cell || !t1->off_x || !t1->off_y))
+        return fail(MD_E_ARG, "mdlg_disp_hist: NULL snapshot array");
+    if (t0->ncell != t1->ncell || t0->h != t1->h || t0->off_is_f64 != t1->off_is_f64)
+        return fail(MD_E_ARG, "mdlg_disp_hist: snapshots differ in ncell, h or offset type");
+    if (t0->ncell < 1 || !(t0->h > 0.0) || (int64_t)t0->ncell * t0->ncell >= (int64_t)1 << 31)
+        return fail(MD_E_ARG, "mdlg_disp_hist: bad ncell or h");
+    if (!(width > 0.0) || !std::isfinite(width)) return fail(MD_E_ARG, "mdlg_disp_hist: width must be > 0");
+    if (nbins < 1 || nbins > PDF_MAX_BINS)
+        return fail(MD_E_ARG, "mdlg_disp_hist: nbins out of [1, %d]", PDF_MAX_BINS);
+    cudaStream_t st = (cudaStream_t)stream;
+    MD_CUDA_TRY(cudaMemsetAsync(hist_out, 0, sizeof(int64_t) * nbins, st));
+    MD_CUDA_TRY(cudaMemsetAsync(outside_out, 0, sizeof(int64_t), st));
+    if (n == 0) return MD_OK;
+    PdfSnap a{t0->cell, t0->off_x, t0->off_y, t0->off_is_f64};
+    PdfSnap b{t1->cell, t1->off_x, t1->off_y, t1->off_is_f64};
+    const double inv_w = 1.0 / width;
+    const size_t smem = sizeof(unsigned) * nbins;
+    if (t0->off_is_f64)
+        k_disp_hist<double><<<pdf_grid(n), 256, smem, st>>>(a, b, (int)n, t0->ncell, t0->h, inv_w, nbins,
+                                                           (unsigned long long *)hist_out,
+                                                           (unsigned long long *)outside_out);
+    else
+        k_disp_hist<float><<<pdf_grid(n), 256, smem, st>>>(a, b, (int)n, t0->ncell, t0->h, inv_w, nbins,
+                                                          (unsigned long long *)hist_out,
+                                                          (unsigned long long *)outside_out);
+    MD_CUDA_TRY(cudaGetLastError());
+    return MD_OK;
+}
+
+extern "C" int disp_pdf_models(double mu2, double lambda, double width, int32_t nbins, double *pg_out,
+                               double *pwsg_out, void *stream) {
+    if (!pg_out || !pwsg_out) return fail(MD_E_ARG, "disp_pdf_models: NULL output");
+    if (!(mu2 > 0.0) || !std::isfinite(mu2)) return fail(MD_E_ARG, "disp_pdf_models: mu2 must be > 0");
+    if (!(lambda >= 0.0) || !(lambda <= 1e5)) return fail(MD_E_ARG, "disp_pdf_models: lambda out of [0, 1e5]");
+    if (!(width > 0.0) || !std::isfinite(width)) return fail(MD_E_ARG, "disp_pdf_models: width must be > 0");
+    if (nbins < 1 || nbins > PDF_MAX_BINS)
+        return fail(MD_E_ARG, "disp_pdf_models: nbins out of [1, %d]", PDF_MAX_BINS);
+    cudaStream_t st = (cudaStream_t)stream;
+    k_pdf_models<<<(nbins + 127) / 128, 128, 0, st>>>(mu2, lambda, width, nbins, pg_out, pwsg_out);
+    MD_CUDA_TRY(cudaGetLastError());
+    return MD_OK;
+}
+
+extern "C" int kl_terms(const double *R, const double *Q, int32_t n, double *K_out, void *stream) {
+    if (!R || !Q || !K_out || n < 0) return fail(MD_E_ARG, "kl_terms: bad arguments");
+    if (n == 0) return MD_OK;
+    k_kl_terms<<<(n + 255) / 256, 256, 0, (cudaStream_t)stream>>>(R, Q, n, K_out);
+    MD_CUDA_TRY(cudaGetLastError());
+    return MD_OK;
+}

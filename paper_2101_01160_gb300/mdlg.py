@@ -90,6 +90,10 @@ _SIGS = {
                   P, P, P, P], C.c_int),
     "mdlg_bin_noalloc": ([C.POINTER(md_snapshot), C.POINTER(md_snapshot), C.c_int64, C.c_int32,
                           C.c_int32, P, P, P, P], C.c_int),
+    "mdlg_disp_hist": ([C.POINTER(md_snapshot), C.POINTER(md_snapshot), C.c_int64, C.c_double,
+                        C.c_int32, P, P, P], C.c_int),
+    "disp_pdf_models": ([C.c_double, C.c_double, C.c_double, C.c_int32, P, P, P], C.c_int),
+    "kl_terms": ([P, P, C.c_int32, P, P], C.c_int),
     "feq_gaussian": ([C.c_double, C.c_double, C.c_double, C.c_int32, P, P], C.c_int),
     "wsg_lambda": ([C.c_double, C.c_double, C.c_int32, P, P], C.c_int),
     "feq_wsg": ([C.c_double, C.c_double, C.c_double, C.c_double, C.c_int32, P, P], C.c_int),
@@ -310,6 +314,41 @@ def mdlg_bin(cell0, ox0, oy0, cell1, ox1, oy1, ncell, h, lx, W, stream=None, noa
     _check(fn(C.byref(s0), C.byref(s1), cell0.numel(), lx, W, _ptr(hist), _ptr(ovf), _ptr(mom),
               _stream(stream)))
     return hist, ovf, mom
+
+
+def disp_hist(cell0, ox0, oy0, cell1, ox1, oy1, ncell, h, width, nbins, stream=None):
+    """Histogram of the continuous per-axis displacement between two device
+    snapshots (Sec. 3(b), Fig. 2): (int64 tensor [nbins], outside count tensor)."""
+    import torch
+
+    f64 = int(ox0.dtype == torch.float64)
+    s0 = md_snapshot(_ptr(cell0).value, _ptr(ox0).value, _ptr(oy0).value, f64, ncell, h)
+    s1 = md_snapshot(_ptr(cell1).value, _ptr(ox1).value, _ptr(oy1).value, f64, ncell, h)
+    hist = torch.empty(nbins, dtype=torch.int64, device="cuda")
+    out = torch.empty(1, dtype=torch.int64, device="cuda")
+    _check(load().mdlg_disp_hist(C.byref(s0), C.byref(s1), cell0.numel(), float(width), int(nbins),
+                                 _ptr(hist), _ptr(out), _stream(stream)))
+    return hist, out
+
+
+def disp_pdf_models(mu2, lam, width, nbins, stream=None):
+    """Gaussian and Poisson-WSG bin masses over the bins of disp_hist."""
+    import torch
+
+    pg = torch.empty(nbins, dtype=torch.float64, device="cuda")
+    pw = torch.empty(nbins, dtype=torch.float64, device="cuda")
+    _check(load().disp_pdf_models(float(mu2), float(lam), float(width), int(nbins), _ptr(pg), _ptr(pw),
+                                  _stream(stream)))
+    return pg, pw
+
+
+def kl_terms(R, Q, stream=None):
+    """K(X_i) of Eq. k_Xi for device float64 tensors R, Q."""
+    import torch
+
+    K = torch.empty_like(R)
+    _check(load().kl_terms(_ptr(R), _ptr(Q), R.numel(), _ptr(K), _stream(stream)))
+    return K
 
 
 def feq_gaussian(a2, ux=0.0, uy=0.0, W=4, stream=None):
