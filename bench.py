@@ -368,7 +368,8 @@ def run_ours(args):
                    "n_particles": ntot, "md_steps_per_step": MD_PER_STEP,
                    "l2": "flushed between timed steps (256 MB write)",
                    "launch_shape": {"block_threads": shape[0], "per_thread": shape[1],
-                                    "staging": "shared" if shape[2] == 1 else "global"},
+                                    "staging": {1: "shared", 2: "global",
+                                                3: "global, full-occupancy registers"}[shape[2]]},
                    "parallelism": f"replicas x{ws}"},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "traffic": _profile_traffic(),

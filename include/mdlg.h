@@ -178,14 +178,17 @@ int md_step(md_system *s, int64_t nsteps);
  * 256), per_thread in [1, 8] particles per thread per chunk (0 = 1),
  * staging 1 = each chunk's neighbour positions, velocities and first list
  * entries are copied to shared memory (double buffered) before its forces
- * are computed, 2 = neighbours are read from global memory through L1
- * (0 = 1).  Results do not depend on the shape: particle order, force
+ * are computed, 2 = neighbours are read from global memory through L1,
+ * 3 = as 2 with the register budget of full occupancy (8 CTAs of 256
+ * threads per SM; FP32 only, in FP64 the same as 2) (0 = 1).  Results do
+ * not depend on the shape: particle order, force
  * summation order and every reduction order are fixed by the data, not by
  * the launch.  Used by md_autotune. */
 int md_tune(md_system *s, int32_t block_threads, int32_t per_thread, int32_t staging);
 
 /* Autotuner: times md_step(steps_per_trial) twice for every launch shape
- * (block {256,128} x per_thread {1,2,4} x staging {1,2}) and keeps the
+ * (block {256,128} x per_thread {1,2,4} x staging {1,2,3}; 3 skipped in
+ * FP64) and keeps the
  * fastest; the choice is cached for the process by (precision, replicas,
  * particle count rounded up to a power of two, list capacity) and reused
  * without trials.  The trial steps are real MD steps: the system advances

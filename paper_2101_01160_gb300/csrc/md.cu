@@ -404,19 +404,24 @@ int dalloc(md_system *s, void **p, size_t bytes) {
     return MD_OK;
 }
 
-const void *persistent_fn(int prec, int block) {
+// staging 3 = global staging with the full-occupancy register budget (FP32
+// only; in FP64 it is the same kernel as staging 2)
+const void *persistent_fn(int prec, int block, int stage) {
     if (prec == MD_FP64)
-        return block == 128 ? (const void *)k_md_persistent<double, 128>
-                            : (const void *)k_md_persistent<double, 256>;
-    return block == 128 ? (const void *)k_md_persistent<float, 128>
-                        : (const void *)k_md_persistent<float, 256>;
+        return block == 128 ? (const void *)k_md_persistent<double, 128, false>
+                            : (const void *)k_md_persistent<double, 256, false>;
+    if (stage == 3)
+        return block == 128 ? (const void *)k_md_persistent<float, 128, true>
+                            : (const void *)k_md_persistent<float, 256, true>;
+    return block == 128 ? (const void *)k_md_persistent<float, 128, false>
+                        : (const void *)k_md_persistent<float, 256, false>;
 }
 
 int configure_launch(md_system *s, int block, int ppt, int stage) {
     if (block != 128 && block != 256) return fail(MD_E_ARG, "block_threads must be 128 or 256");
     if (ppt < 1 || ppt > 8) return fail(MD_E_ARG, "per_thread must be in [1, 8]");
-    if (stage != 1 && stage != 2) return fail(MD_E_ARG, "staging must be 1 or 2");
-    const void *fn = persistent_fn(s->prec, block);
+    if (stage < 1 || stage > 3) return fail(MD_E_ARG, "staging must be 1, 2 or 3");
+    const void *fn = persistent_fn(s->prec, block, stage);
     const int chunk = ppt * block;
     // chunk table: ppt*block consecutive slots of one replica
     std::vector<int4> ch;
@@ -427,8 +432,8 @@ int configure_launch(md_system *s, int block, int ppt, int stage) {
     }
     if ((long long)ch.size() > s->chunk_cap) return fail(MD_E_LIMIT, "chunk table overflow");
     const long long nch = (long long)ch.size();
-    const size_t smem = s->prec == MD_FP64 ? smem_bytes<double>(s->n_lg, s->n_dx, s->nb, chunk)
-                                           : smem_bytes<float>(s->n_lg, s->n_dx, s->nb, chunk);
+    const size_t smem = s->prec == MD_FP64 ? smem_bytes<double>(s->n_lg, s->n_dx, s->nb, chunk, stage == 1)
+                                           : smem_bytes<float>(s->n_lg, s->n_dx, s->nb, chunk, stage == 1);
     if (smem > 227 * 1024) return fail(MD_E_LIMIT, "shared memory per CTA exceeds 227 KB");
     MD_CUDA_TRY(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     int occ = 0;
@@ -478,7 +483,7 @@ int configure_launch(md_system *s, int block, int ppt, int stage) {
 }
 
 int launch_persistent(md_system *s, long long nsteps, int force_rebuild) {
-    const void *fn = persistent_fn(s->prec, s->block);
+    const void *fn = persistent_fn(s->prec, s->block, s->stage);
     long long step0 = s->step;
     int phase = s->phase_half;
     void *args[] = {&s->sd, &step0, &nsteps, &phase, &force_rebuild};
@@ -1061,11 +1066,12 @@ int md_autotune(md_system *s, int64_t steps_per_trial, int32_t *best3) {
     MD_CUDA_TRY(cudaEventCreate(&e1));
     float best_ms = 1e30f;
     int bb = 256, bp = 1, bs = 1;
-    const int blocks[2] = {256, 128}, ppts[3] = {1, 2, 4}, stages[2] = {1, 2};
+    const int blocks[2] = {256, 128}, ppts[3] = {1, 2, 4}, stages[3] = {1, 2, 3};
     int rc = MD_OK;
     for (int b : blocks)
         for (int p : ppts)
             for (int st : stages) {
+                if (st == 3 && s->prec == MD_FP64) continue;               // same kernel as 2
                 if (configure_launch(s, b, p, st) != MD_OK) continue;   // shape does not fit
                 rc = md_step(s, steps_per_trial);                          // settles caches
                 if (rc) break;

@@ -686,9 +686,11 @@ __device__ inline Stage<T> stage_at(unsigned char *p, int chunk) {
     return B;
 }
 template <typename T>
-__host__ __device__ inline size_t smem_bytes(int n_lg, int n_dx, int nb, int chunk) {
+__host__ __device__ inline size_t smem_bytes(int n_lg, int n_dx, int nb, int chunk, bool staged) {
+    // the two staging buffers exist only when chunks are staged in shared
+    // memory; without them more CTAs fit on an SM
     return smem_hist_bytes(n_lg, n_dx, nb) + align16(MAX_CPC * sizeof(ChunkDesc)) +
-           2 * stage_bytes<T>(chunk);
+           (staged ? 2 * stage_bytes<T>(chunk) : 0);
 }
 
 // Velocity-Verlet update of one particle: v += (dt/2m) F twice (the first
@@ -729,8 +731,15 @@ __device__ __forceinline__ void kick_drift(const RepDev &R, typename V2<T>::type
 //   rebuild (cell list + neighbour lists) once the accumulated bound on
 //     displacements since the last rebuild reaches half the skin: until then
 //     no pair can have come within rc without being listed.
-template <typename T, int BLOCK>
-__global__ void __launch_bounds__(BLOCK, BLOCK == 256 ? 4 : 8) k_md_persistent(SysDev S, long long step0,
+// CTAs per SM the register allocation is sized for: half occupancy (64
+// registers), or with DENSE full occupancy (32 registers: the spills cost
+// less than the extra latency hiding gains on large ensembles, whose
+// neighbour gathers also use the L1 left free when chunks are not staged;
+// small systems prefer the former).  The autotuner chooses.
+constexpr int md_min_ctas(int block, bool dense) { return (dense ? 2048 : 1024) / block; }
+
+template <typename T, int BLOCK, bool DENSE>
+__global__ void __launch_bounds__(BLOCK, md_min_ctas(BLOCK, DENSE)) k_md_persistent(SysDev S, long long step0,
                                                                            long long nsteps,
                                                                            int phase_half,
                                                                            int force_rebuild) {

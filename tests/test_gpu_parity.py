@@ -358,7 +358,8 @@ def test_results_independent_of_launch_shape(mdlg):
     p = mdlg.make_params(n, L, precision=mdlg.MD_FP32_CELLOFF, lg_every=(100, 300),
                          lx=(int(L), int(L / 2)))
     out = []
-    for block, ppt, staging in ((256, 1, 1), (128, 4, 1), (256, 8, 2), (128, 1, 2)):
+    for block, ppt, staging in ((256, 1, 1), (128, 4, 1), (256, 8, 2), (128, 1, 2), (256, 1, 3),
+                                (128, 2, 3)):
         s = mdlg.System(p, st.x, st.y, st.vx, st.vy)
         s.tune(block, ppt, staging)
         s.step(900)
