@@ -126,6 +126,9 @@ __device__ __forceinline__ double inv_r2(double r2) { return 1.0 / r2; }
 // observation kernel produce identical bits.
 __device__ __forceinline__ float fmaT(float a, float b, float c) { return __fmaf_rn(a, b, c); }
 __device__ __forceinline__ double fmaT(double a, double b, double c) { return __fma_rn(a, b, c); }
+// a + b c with the product and the sum rounded separately, never contracted
+__device__ __forceinline__ float axpyT(float a, float b, float c) { return __fadd_rn(a, __fmul_rn(b, c)); }
+__device__ __forceinline__ double axpyT(double a, double b, double c) { return __dadd_rn(a, __dmul_rn(b, c)); }
 
 // One pair: separation (rx, ry) = x_j - x_i; accumulates the force on i.
 // Written with explicit fused multiply-adds so that every caller evaluates
@@ -314,6 +317,7 @@ __device__ __forceinline__ int own_chunks(int nchunks) {
     return nchunks > (int)blockIdx.x ? (nchunks - (int)blockIdx.x + (int)gridDim.x - 1) / (int)gridDim.x : 0;
 }
 __device__ __forceinline__ int own_chunk(int i) { return (int)blockIdx.x + i * (int)gridDim.x; }
+
 
 // ---------------------------------------------------------------- neighbour lists
 // Builds the list of slot i from the 3x3 cell stencil (same row/cell order
@@ -703,18 +707,21 @@ __device__ __forceinline__ void kick_drift(const RepDev &R, typename V2<T>::type
                                            bool first, float vscale, typename V2<T>::type *pout,
                                            typename V2<T>::type *vel, int slot, float &vm,
                                            bool &bad) {
+    // explicit roundings (no contraction), so that every call site gives the
+    // same bits (FMA contraction would otherwise be decided per call site)
     if (!first) {
-        v.x = v.x + hk * fx;
-        v.y = v.y + hk * fy;
+        v.x = axpyT(v.x, hk, fx);
+        v.y = axpyT(v.y, hk, fy);
     }
-    v.x = v.x + hk * fx;
-    v.y = v.y + hk * fy;
+    v.x = axpyT(v.x, hk, fx);
+    v.y = axpyT(v.y, hk, fy);
     typename V2<T>::type on;
-    on.x = oi.x + dt * v.x;
-    on.y = oi.y + dt * v.y;
+    on.x = axpyT(oi.x, dt, v.x);
+    on.y = axpyT(oi.y, dt, v.y);
     pout[slot] = on;
     vel[slot] = v;
-    const float sp = sqrtf((float)(v.x * v.x + v.y * v.y)) * vscale;
+    const float vx = (float)v.x, vy = (float)v.y;
+    const float sp = __fmul_rn(sqrtf(__fmaf_rn(vx, vx, __fmul_rn(vy, vy))), vscale);
     vm = fmaxf(vm, sp);
     bad |= !(sp < 1e30f);   // non-finite velocity
 }
@@ -958,8 +965,8 @@ __global__ void k_observe(SysDev S, ObsArgs A) {
             lj_stencil<T, true>(R, pos, S.cell_start, cpk, oi, slot, fx, fy, pe, fa);
             if (A.complete) {
                 const T hk = rd<T>(R.hk, R.hkf);
-                v.x = v.x + hk * fx;
-                v.y = v.y + hk * fy;
+                v.x = axpyT(v.x, hk, fx);
+                v.y = axpyT(v.y, hk, fy);
                 vel[slot] = v;
             }
             ke = 0.5 * R.mass * ((double)v.x * (double)v.x + (double)v.y * (double)v.y);
