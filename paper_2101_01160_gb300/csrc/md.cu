@@ -440,8 +440,12 @@ int configure_launch(md_system *s, int block, int ppt, int stage) {
     MD_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, block, smem));
     if (occ < 1) return fail(MD_E_CUDA, "persistent kernel does not fit on an SM");
     const long long maxco = (long long)occ * s->nsm;
+    // Every SM gets the same number of CTAs (the full resident grid, unless
+    // there are fewer chunks): an SM finishes a step's force pass when all of
+    // its CTAs' work is done, so an SM with one CTA more would set the pace
+    // of the grid barrier.  The chunk dealing below evens out the per-CTA sums.
     const long long q = (nch + maxco - 1) / maxco;
-    const long long grid = std::min<long long>(4096, std::max<long long>(1, (nch + q - 1) / q));
+    const long long grid = std::min<long long>(4096, std::max<long long>(1, std::min<long long>(maxco, nch)));
     if (q > MAX_CPC) return fail(MD_E_LIMIT, "more than %d chunks per CTA: raise per_thread", MAX_CPC);
     // CTA b owns table entries b, b + grid, b + 2 grid, ...  Chunks differ in
     // cost by the replicas' densities (neighbours per particle), so they are
