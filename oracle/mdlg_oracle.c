@@ -27,6 +27,10 @@
  *   or_wsg_lambda                the roots lambda_{1,2} of Eq. (lambda_eq)
  *   or_wsg_mu4                   Eq. (fourth_order)
  *   or_kl                        Eq. (kullback_leibler) / Eq. (k_Xi)
+ *   or_site_occupation           the local occupation numbers n_i(x, t) of
+ *                                Eq. (n_i) per lattice site (Sec. 2)
+ *   or_collision                 the lattice-gas collision operator Xi_i of
+ *                                Eq. (mdlg_evolution) (Sec. 2)
  *   or_disp_hist                 histogram of the continuous one-dimensional
  *                                displacement component over bins X_i (the
  *                                measured PDF of Sec. 3(b), Fig. 2)
@@ -53,8 +57,10 @@
  * Eq. (fourth_order), lambda1*lambda2 = 1, the LJ force against a finite
  * difference of the potential and known potential values, Newton's third law,
  * the cell list against all pairs, NVE energy drift scaling as dt^2, exact
- * time reversal, and the ballistic ideal gas against the Gaussian
- * equilibrium.  Parity of the measured f_eq of the interacting gas has no
+ * time reversal, the ballistic ideal gas against the Gaussian equilibrium,
+ * the local occupation numbers against their indicator sum and the global
+ * histogram, and mass conservation and free streaming of the collision
+ * operator.  Parity of the measured f_eq of the interacting gas has no
  * printed values to pin to (the paper ships no data): only statistical
  * agreement and the qualitative claims of Sec. 5 are checked.
  */
@@ -150,6 +156,62 @@ int or_bin_celloff(int64_t n, const int32_t *c0, const void *ox0, const void *oy
     or_bin_xy(n, b, b + n, b + 2 * n, b + 3 * n, L, lx, W, hist, overflow, mom);
     free(b);
     return 0;
+}
+
+/* Local occupation numbers of Eq. (n_i), Sec. 2: n_i(x, t1) counts the
+ * particles that are in lattice cell x at t1 and were in cell x - v_i at t0
+ * (v_i taken as the nearest periodic image of the lattice displacement).
+ * nfield has (2W+1)^2 * lx^2 entries, class-major: class i = (vy+W)(2W+1) +
+ * (vx+W), site x = ly*lx + lx_; a particle whose displacement leaves the
+ * window counts in ovf[x] of its arrival site, so that summed over x and i
+ * this is or_bin_celloff's histogram.  Accumulates. */
+int or_site_occupation(int64_t n, const int32_t *c0, const void *ox0, const void *oy0,
+                       const int32_t *c1, const void *ox1, const void *oy1, int32_t f64,
+                       int32_t ncell, double h, double L, int64_t lx, int32_t W,
+                       int64_t *nfield, int64_t *ovf)
+{
+    double *b = (double *)malloc(sizeof(double) * 4 * (size_t)(n > 0 ? n : 1));
+    if (!b) return -1;
+    decode(n, c0, ox0, oy0, f64, ncell, h, b, b + n);
+    decode(n, c1, ox1, oy1, f64, ncell, h, b + 2 * n, b + 3 * n);
+    double dxl = L / (double)lx;
+    int64_t side = 2 * (int64_t)W + 1;
+    int64_t nsite = lx * lx;
+    for (int64_t j = 0; j < n; ++j) {
+        int64_t sx0 = lattice_index(b[j], dxl, lx);
+        int64_t sy0 = lattice_index(b[n + j], dxl, lx);
+        int64_t sx1 = lattice_index(b[2 * n + j], dxl, lx);
+        int64_t sy1 = lattice_index(b[3 * n + j], dxl, lx);
+        int64_t vx = nearest_image_int(sx1 - sx0, lx);
+        int64_t vy = nearest_image_int(sy1 - sy0, lx);
+        int64_t site = sy1 * lx + sx1;
+        if (vx >= -W && vx <= W && vy >= -W && vy <= W)
+            nfield[((vy + W) * side + (vx + W)) * nsite + site] += 1;
+        else
+            ovf[site] += 1;
+    }
+    free(b);
+    return 0;
+}
+
+/* Lattice-gas collision operator of Eq. (mdlg_evolution), Sec. 2:
+ * Xi_i(x, t) = n_i(x + v_i, t + dt) - n_i(x, t), x + v_i periodic, for the
+ * occupation fields nt = n(., t) and nn = n(., t + dt) in the layout of
+ * or_site_occupation. */
+void or_collision(const int64_t *nt, const int64_t *nn, int64_t lx, int32_t W, int64_t *xi)
+{
+    int64_t side = 2 * (int64_t)W + 1;
+    int64_t nsite = lx * lx;
+    for (int64_t vy = -W; vy <= W; ++vy)
+        for (int64_t vx = -W; vx <= W; ++vx) {
+            int64_t i = (vy + W) * side + (vx + W);
+            for (int64_t y = 0; y < lx; ++y)
+                for (int64_t x = 0; x < lx; ++x) {
+                    int64_t xd = ((x + vx) % lx + lx) % lx;
+                    int64_t yd = ((y + vy) % lx + lx) % lx;
+                    xi[i * nsite + y * lx + x] = nn[i * nsite + yd * lx + xd] - nt[i * nsite + y * lx + x];
+                }
+        }
 }
 
 /* Histogram of the continuous one-dimensional displacement component over

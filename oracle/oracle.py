@@ -77,6 +77,10 @@ def _declare(L):
     L.or_kl.restype = D
     L.or_kl_terms.argtypes = [P, P, I64, P]
     L.or_kl_terms.restype = None
+    L.or_site_occupation.argtypes = [I64, P, P, P, P, P, P, I32, I32, D, D, I64, I32, P, P]
+    L.or_site_occupation.restype = C.c_int
+    L.or_collision.argtypes = [P, P, I64, I32, P]
+    L.or_collision.restype = None
     L.or_disp_hist.argtypes = [I64, P, P, P, P, P, P, I32, I32, D, D, D, I32, P, P]
     L.or_disp_hist.restype = C.c_int
     L.or_pdf_gauss_bins.argtypes = [D, D, I32, P]
@@ -134,6 +138,34 @@ def bin_celloff(s, ncell, h, L, lx, W):
                               _p(hist), _p(ovf), _p(mom))
     assert rc == 0
     return hist, int(ovf[0]), mom
+
+
+def site_occupation(s, ncell, h, L, lx, W):
+    """Local occupation numbers of Eq. (n_i) for the snapshot pair s (t0 ->
+    t1): returns (n int64[(2W+1)^2, lx, lx] indexed [class][ly][lx], ovf
+    int64[lx, lx]) at the arrival sites."""
+    f64 = s["ox0"].dtype == np.float64
+    ft = np.float64 if f64 else np.float32
+    arrs = [np.ascontiguousarray(s[k], dtype=(np.int32 if k.startswith("cell") else ft))
+            for k in ("cell0", "ox0", "oy0", "cell1", "ox1", "oy1")]
+    n = len(arrs[0])
+    nb = (2 * W + 1) ** 2
+    nf = np.zeros((nb, lx, lx), np.int64)
+    ovf = np.zeros((lx, lx), np.int64)
+    rc = lib().or_site_occupation(n, *[_p(a) for a in arrs], int(f64), ncell, h, L, lx, W,
+                                  _p(nf), _p(ovf))
+    assert rc == 0
+    return nf, ovf
+
+
+def collision(nt, nn, W):
+    """Collision operator Xi of Eq. (mdlg_evolution) from the occupation
+    fields at t and t + dt (layout of site_occupation)."""
+    nt = np.ascontiguousarray(nt, dtype=np.int64)
+    nn = np.ascontiguousarray(nn, dtype=np.int64)
+    xi = np.zeros_like(nt)
+    lib().or_collision(_p(nt), _p(nn), nt.shape[-1], W, _p(xi))
+    return xi
 
 
 def disp_hist(s, ncell, h, L, width, nbins):

@@ -133,6 +133,43 @@ def random_celloff_snapshots(n: int, ncell: int, h: float, seed: int, max_step: 
     )
 
 
+def random_celloff_walk(n: int, ncell: int, h: float, seed: int, max_step: float, steps: int,
+                        f64: bool = False):
+    """``steps`` + 1 snapshots of a random walk in the (linear cell index,
+    in-cell offset) encoding: uniform start, then per snapshot a uniform
+    displacement of at most ``max_step`` per axis, re-expressed in the cell it
+    lands in with offsets up to 0.25 h outside [0, h) (a stale cell list).
+    Returns a list of dict(cell, ox, oy)."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    ft = np.float64 if f64 else np.float32
+    L = ncell * h
+    X = rng.uniform(0.0, L, n)
+    Y = rng.uniform(0.0, L, n)
+    out = []
+    for k in range(steps + 1):
+        if k:
+            X = np.mod(X + rng.uniform(-max_step, max_step, n), L)
+            Y = np.mod(Y + rng.uniform(-max_step, max_step, n), L)
+        sx = rng.uniform(-0.25, 0.25, n) * h
+        sy = rng.uniform(-0.25, 0.25, n) * h
+        cx = np.floor((X - sx) / h).astype(np.int64)
+        cy = np.floor((Y - sy) / h).astype(np.int64)
+        ox = (X - cx * h).astype(ft)
+        oy = (Y - cy * h).astype(ft)
+        out.append(dict(cell=((cy % ncell) * ncell + (cx % ncell)).astype(np.int32), ox=ox, oy=oy))
+    return out
+
+
+def shear_wave_state(n: int, L: float, T: float, U: float, seed: int) -> State:
+    """lattice_gas_state with a transverse sine flow added: vx += U sin(2 pi
+    y / L) (one wavelength over the box), less its mean so that the total
+    momentum stays zero."""
+    st = lattice_gas_state(n, L, T, seed)
+    w = U * np.sin(2.0 * np.pi * st.y / L)
+    st.vx = st.vx + (w - w.mean())
+    return st
+
+
 def ensemble_params(n_rep: int, seed: int, n_min: int = 4096, n_max: int = 65536,
                     phi_lo: float = 0.02, phi_hi: float = 0.30, T_lo: float = 1.0,
                     T_hi: float = 20.0):
