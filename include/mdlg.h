@@ -297,6 +297,40 @@ int mdlg_bin(const md_snapshot *t0, const md_snapshot *t1, int64_t n, int32_t lx
 int mdlg_bin_noalloc(const md_snapshot *t0, const md_snapshot *t1, int64_t n, int32_t lx, int32_t W,
                      int32_t *hist_out, int64_t *overflow_out, double *mom_out, void *stream);
 
+/* ---- local MDLG fields (Sec. 2, Eqs. n_i and mdlg_evolution) ------------ */
+
+/* Local occupation numbers of Eq. (n_i): n_i(x, t1) is the number of
+ * particles in lattice site x at t1 that were in site x - v_i at t0.  Sites
+ * and the lattice displacement v_i are those of mdlg_bin (l = floor(x /
+ * dxl) mod lx per axis, dxl = ncell*h/lx, nearest periodic image of
+ * l1 - l0), so the field summed over its sites is mdlg_bin's histogram and
+ * its overflow summed is mdlg_bin's overflow, bit for bit.
+ * n_out: device int32 [(2W+1)^2][lx][lx], class-major, entry
+ * ((vy+W)(2W+1) + (vx+W)) lx^2 + ly lx + lx_ at the arrival site (lx_, ly);
+ * overflow_out: device int32 [lx][lx], particles arriving at a site whose
+ * displacement leaves the window.  Both are ADDED TO (clear them first): a
+ * call over a snapshot pair that concatenates R replicas of one box, or R
+ * calls, leave the ensemble sum, and f_i = <n_i> of the MDLB (Sec. 2) is
+ * that sum over R.  Counts are exact; the caller keeps each entry below
+ * 2^31.  n < 2^31, 1 <= lx, 0 <= W <= MD_MAX_W, (2W+1)^2 lx^2 < 2^31
+ * (MD_E_LIMIT).  Asynchronous on stream. */
+int mdlg_site_occupation(const md_snapshot *t0, const md_snapshot *t1, int64_t n, int32_t lx,
+                         int32_t W, int32_t *n_out, int32_t *overflow_out, void *stream);
+
+/* Lattice-gas collision operator of Eq. (mdlg_evolution):
+ * Xi_i(x, t) = n_i(x + v_i, t + dt) - n_i(x, t), x + v_i periodic on the
+ * lx x lx lattice, from the fields n_t = n(., t) and n_next = n(., t + dt)
+ * in the layout of mdlg_site_occupation (the window t -> t + dt must start
+ * at the snapshot that ended the window of n_t).  xi_out (int32) and/or
+ * omega_out (double, scale * Xi; with fields summed over R replicas and
+ * scale = 1/R this is the MDLB collision operator Omega_i = <Xi_i>) are
+ * overwritten; either may be NULL, not both.  All device memory, same
+ * shape as the fields.  Summed over i, Xi vanishes at every site when no
+ * displacement of either window left the window W.  Asynchronous on
+ * stream. */
+int mdlg_collision(const int32_t *n_t, const int32_t *n_next, int32_t lx, int32_t W, double scale,
+                   int32_t *xi_out, double *omega_out, void *stream);
+
 /* ---- displacement-PDF diagnostics (Sec. 3(b), Fig. 2) -------------------- */
 
 /* Histogram of the continuous one-dimensional displacement component between

@@ -26,7 +26,7 @@ __device__ __forceinline__ double snap_off(const void *p, int f64, int j) {
 }
 
 __global__ void k_bin_snapshots(SnapDev s0, SnapDev s1, int n, int ncell, double h, double L,
-                                int lx, double dxl, int W, int *hist,
+                                int lx, double dxl, double inv, int W, int *hist,
                                 unsigned long long *ovf, double *part) {
     extern __shared__ int sh[];
     const int side = 2 * W + 1, nb = side * side;
@@ -50,8 +50,10 @@ __global__ void k_bin_snapshots(SnapDev s0, SnapDev s1, int n, int ncell, double
             const double y0 = cell_position(cy0, h, snap_off(s0.oy, s0.f64, j));
             const double x1 = cell_position(cx1, h, snap_off(s1.ox, s1.f64, j));
             const double y1 = cell_position(cy1, h, snap_off(s1.oy, s1.f64, j));
-            const long long ddx = lattice_shift(lattice_cell(x1, dxl, lx) - lattice_cell(x0, dxl, lx), lx);
-            const long long ddy = lattice_shift(lattice_cell(y1, dxl, lx) - lattice_cell(y0, dxl, lx), lx);
+            const long long ddx = lattice_shift(
+                lattice_cell_mul(x1, dxl, inv, lx) - lattice_cell_mul(x0, dxl, inv, lx), lx);
+            const long long ddy = lattice_shift(
+                lattice_cell_mul(y1, dxl, inv, lx) - lattice_cell_mul(y0, dxl, inv, lx), lx);
             if (ddx >= -W && ddx <= W && ddy >= -W && ddy <= W)
                 bin = (int)((ddy + W) * side + (ddx + W));
             else
@@ -122,7 +124,7 @@ int bin_launch(const md_snapshot *t0, const md_snapshot *t1, int64_t n, int32_t 
     const double L = (double)t0->ncell * t0->h;
     const double dxl = L / (double)lx;
     k_bin_snapshots<<<grid, 256, nb * sizeof(int), st>>>(a, b, (int)n, t0->ncell, t0->h, L, lx, dxl,
-                                                        W, hist_out,
+                                                        1.0 / dxl, W, hist_out,
                                                         (unsigned long long *)overflow_out, part);
     MD_CUDA_TRY(cudaGetLastError());
     k_sum_partials<<<1, 32, 0, st>>>(part, grid, mom_out);

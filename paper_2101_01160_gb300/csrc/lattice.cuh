@@ -24,6 +24,94 @@ __device__ __forceinline__ long long lattice_cell(double x, double dxl, int lx) 
     return l;
 }
 
+// The same lattice cell, floor(RN(x / dxl)) mod lx, with the division
+// replaced by a product with inv = RN(1 / dxl) wherever that cannot change
+// the result.  q = RN(x * inv) and RN(x / dxl) both lie within |q| 2^-51 of
+// the exact quotient x / dxl (each is one or two roundings of relative size
+// 2^-53 away from it), so when q is more than |q| 2^-50 from the nearest
+// integer no integer separates them and floor(q) is the answer; otherwise
+// (points on or next to a lattice line, x = 0, and |q| < 2^-900, where
+// underflow would void the relative bounds) the division is done.
+// Bit-identical to lattice_cell for every finite x; one FP64 product, a rint
+// and a compare in place of a division on all but those cases.
+__device__ __forceinline__ long long lattice_cell_mul(double x, double dxl, double inv, int lx) {
+    const double q = __dmul_rn(x, inv);
+    const double t = rint(q);
+    const double fq = fabs(q);
+    double f;
+    if (fq > 0x1p-900 && fabs(__dsub_rn(q, t)) > __dmul_rn(fq, 0x1p-50))
+        f = floor(q);
+    else
+        f = floor(__ddiv_rn(x, dxl));
+    long long l = (long long)f;
+    l %= lx;
+    if (l < 0) l += lx;
+    return l;
+}
+
+// The lattice cell of the position encoded as (cell coordinate c, offset
+// off), floor(RN(RN(c*h + off) / dxl)) mod lx as lattice_cell computes it,
+// decided in FP32 wherever FP32 provably gives the same cell.  With a =
+// RN32(c * hf), hf = RN32(h), invf = RN32(1/dxl):
+//     q = RN32(RN32(a + off) * invf),   S = RN32(RN32(|a| + |off|) * invf),
+// the distance of q from the exact quotient (c*h + off)/dxl is below
+// S 2^-21 (a: two roundings of c*h, the sum one, the offset one if it is
+// FP64, the product two -- each at most 2^-24 relative to |a| + |off|), and
+// the FP64 reference lies within a few 2^-53 relative of the same quotient.
+// So when q is more than S 2^-20 from the nearest integer, floor(q) is the
+// cell; otherwise (points on or within about S 1e-6 of a lattice line) the
+// FP64 evaluation of lattice_cell decides.  Bit-identical to lattice_cell
+// for every finite encoded position; in the common case a few FP32 and
+// 32-bit integer operations replace the FP64 ones and the 64-bit modulo
+// (GB300's FP64 rate is a small fraction of its FP32 rate).  lx < 2^22.
+template <typename T>
+__device__ __forceinline__ int lattice_cell_f32(int c, T off, double h, float hf, double dxl, float invf,
+                                                int lx) {
+    const float a = __fmul_rn((float)c, hf);
+    const float o = (float)off;
+    const float q = __fmul_rn(__fadd_rn(a, o), invf);
+    const float S = __fmul_rn(__fadd_rn(fabsf(a), fabsf(o)), invf);
+    if (S < 0x1p22f && fabsf(__fsub_rn(q, rintf(q))) > __fmul_rn(S, 0x1p-20f)) {
+        int l = (int)floorf(q);
+        // positions within a box edge of the box need one wrap; others the
+        // general reduction
+        if (l < 0) l += lx;
+        else if (l >= lx) l -= lx;
+        if (l < 0 || l >= lx) {
+            l %= lx;
+            if (l < 0) l += lx;
+        }
+        return l;
+    }
+    return (int)lattice_cell(cell_position(c, h, (double)off), dxl, lx);
+}
+
+// Splits a linear cell index c = cy * ncell + cx (0 <= cx, cy < ncell,
+// ncell^2 < 2^31) without an integer division: the float estimate of
+// c / ncell (< 46341) carries a relative error below 2^-22, so it is off by
+// at most one, and one multiply-subtract with a fix-up makes it exact.
+__device__ __forceinline__ void split_cell(int c, int ncell, float inv_ncell, int &cx, int &cy) {
+    int y = (int)__fmul_rz((float)c, inv_ncell);
+    int x = c - y * ncell;
+    if (x < 0) {
+        --y;
+        x += ncell;
+    } else if (x >= ncell) {
+        ++y;
+        x -= ncell;
+    }
+    cx = x;
+    cy = y;
+}
+
+// Nearest periodic image of a lattice displacement d in (-lx, lx) (two
+// cells of [0, lx)), in (-lx/2, lx/2]: lattice_shift without the modulo.
+__device__ __forceinline__ int lattice_shift_near(int d, int lx) {
+    if (d < 0) d += lx;
+    if (d > lx / 2) d -= lx;
+    return d;
+}
+
 // Lattice displacement reduced to the nearest periodic image, in
 // (-lx/2, lx/2].
 __device__ __forceinline__ long long lattice_shift(long long d, int lx) {

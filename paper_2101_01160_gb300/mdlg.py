@@ -92,6 +92,9 @@ _SIGS = {
                           C.c_int32, P, P, P, P], C.c_int),
     "mdlg_disp_hist": ([C.POINTER(md_snapshot), C.POINTER(md_snapshot), C.c_int64, C.c_double,
                         C.c_int32, P, P, P], C.c_int),
+    "mdlg_site_occupation": ([C.POINTER(md_snapshot), C.POINTER(md_snapshot), C.c_int64, C.c_int32,
+                              C.c_int32, P, P, P], C.c_int),
+    "mdlg_collision": ([P, P, C.c_int32, C.c_int32, C.c_double, P, P, P], C.c_int),
     "disp_pdf_models": ([C.c_double, C.c_double, C.c_double, C.c_int32, P, P, P], C.c_int),
     "kl_terms": ([P, P, C.c_int32, P, P], C.c_int),
     "feq_gaussian": ([C.c_double, C.c_double, C.c_double, C.c_int32, P, P], C.c_int),
@@ -329,6 +332,45 @@ def disp_hist(cell0, ox0, oy0, cell1, ox1, oy1, ncell, h, width, nbins, stream=N
     _check(load().mdlg_disp_hist(C.byref(s0), C.byref(s1), cell0.numel(), float(width), int(nbins),
                                  _ptr(hist), _ptr(out), _stream(stream)))
     return hist, out
+
+
+def site_occupation(cell0, ox0, oy0, cell1, ox1, oy1, ncell, h, lx, W, field=None, ovf=None,
+                    stream=None):
+    """Local occupation numbers n_i(x, t1) of Eq. n_i between two device
+    snapshots: (int32 field [(2W+1)^2, lx, lx], int32 overflow [lx, lx]).
+    Given `field` / `ovf` tensors are added to (ensemble or window sums);
+    otherwise zeroed ones are made."""
+    import torch
+
+    f64 = int(ox0.dtype == torch.float64)
+    s0 = md_snapshot(_ptr(cell0).value, _ptr(ox0).value, _ptr(oy0).value, f64, ncell, h)
+    s1 = md_snapshot(_ptr(cell1).value, _ptr(ox1).value, _ptr(oy1).value, f64, ncell, h)
+    q = (2 * W + 1) ** 2
+    if field is None:
+        field = torch.zeros((q, lx, lx), dtype=torch.int32, device="cuda")
+    if ovf is None:
+        ovf = torch.zeros((lx, lx), dtype=torch.int32, device="cuda")
+    _check(load().mdlg_site_occupation(C.byref(s0), C.byref(s1), cell0.numel(), int(lx), int(W),
+                                       _ptr(field), _ptr(ovf), _stream(stream)))
+    return field, ovf
+
+
+def collision(n_t, n_next, W, scale=None, stream=None):
+    """Collision operator of Eq. mdlg_evolution from two occupation fields:
+    the int32 Xi field, or, with `scale` given, the float64 scale * Xi (the
+    ensemble-averaged Omega for fields summed over 1/scale replicas)."""
+    import torch
+
+    lx = n_t.shape[-1]
+    if scale is None:
+        out = torch.empty_like(n_t)
+        _check(load().mdlg_collision(_ptr(n_t), _ptr(n_next), int(lx), int(W), 1.0, _ptr(out), None,
+                                     _stream(stream)))
+    else:
+        out = torch.empty(n_t.shape, dtype=torch.float64, device=n_t.device)
+        _check(load().mdlg_collision(_ptr(n_t), _ptr(n_next), int(lx), int(W), float(scale), None,
+                                     _ptr(out), _stream(stream)))
+    return out
 
 
 def disp_pdf_models(mu2, lam, width, nbins, stream=None):
