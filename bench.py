@@ -231,6 +231,51 @@ def _time_disp_hist(mdlg, torch, n=1 << 24, reps=5):
             "workload": "synthetic FP32 snapshot pair, 16.8M particles, 512 bins of 0.05 sigma"}
 
 
+def _time_local_fields(mdlg, torch, reps=10):
+    """Local MDLG fields (Sec. 2, Eqs. n_i and mdlg_evolution) of a synthetic
+    ensemble snapshot pair: 64 replicas of the standard system's box (N =
+    99,856, L = 1000) in one call, on Table 1's lx = 250 lattice, W = 4.  L2
+    is flushed before every timed launch.  Algorithmic traffic: 24 B per
+    particle for the occupation numbers (two FP32 snapshots; the 20 MB field
+    stays in L2), 12 B per field entry for the collision operator (two int32
+    fields read, one written)."""
+    from paper_2101_01160_gb300 import inputs
+
+    n, ncell, lx, W = 64 * 99_856, 333, 250, 4
+    h = float(np.float32(1000.0 / ncell))
+    s = inputs.random_celloff_snapshots(n, ncell, h, seed=77, max_step=4.0, lattice_dx=ncell * h / lx)
+    d = [torch.from_numpy(s[k]).cuda() for k in ("cell0", "ox0", "oy0", "cell1", "ox1", "oy1")]
+    field, ovf = mdlg.site_occupation(*d, ncell, h, lx, W)
+    f2, _ = mdlg.site_occupation(*d, ncell, h, lx, W)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    out = {}
+    for name, fn in (("occupation", lambda: mdlg.site_occupation(*d, ncell, h, lx, W, field=field, ovf=ovf)),
+                     ("collision", lambda: mdlg.collision(field, f2, W))):
+        for _ in range(3):
+            fn()
+        ms = []
+        for _ in range(reps):
+            flush.zero_()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            fn()
+            e1.record()
+            torch.cuda.synchronize()
+            ms.append(e0.elapsed_time(e1))
+        out[name] = float(np.median(ms))
+    peak, kind = _peaks()
+    entries = (2 * W + 1) ** 2 * lx * lx
+    g_occ = 24.0 * n / (out["occupation"] * 1e-3) / 1e9
+    g_col = 12.0 * entries / (out["collision"] * 1e-3) / 1e9
+    return {"particles": n, "field_entries": entries,
+            "occupation": {"kernel": "k_site_occupation", "ms_per_launch": out["occupation"], "gbs": g_occ,
+                           "frac": g_occ / peak, "bytes_per_particle": 24},
+            "collision": {"kernel": "k_collision", "ms_per_launch": out["collision"], "gbs": g_col,
+                          "frac": g_col / peak, "bytes_per_entry": 12},
+            "peak_gbs": peak, "peak_kind": kind,
+            "workload": "synthetic FP32 ensemble snapshot pair, 64 x 99,856 particles, L = 1000, lx = 250, W = 4"}
+
+
 def run_profile_case(args):
     """Small cases for ncu captures (not a bench line): md64 = the first 64
     replicas of the batched ensemble (about 1.4M particles, > L2), fixed
@@ -238,7 +283,9 @@ def run_profile_case(args):
     full-occupancy register budget, as the autotuner picks for the bench), two
     400-step warm-up launches then three 100-step launches; mlp = three fused
     surrogate forward passes on 1M queries; disp = eight displacement-PDF
-    histograms of a 16.8M-particle snapshot pair."""
+    histograms of a 16.8M-particle snapshot pair; local = the occupation and
+    collision kernels of the local fields on a 6.4M-particle ensemble snapshot
+    pair (five launches each after two occupation calls)."""
     import torch
 
     from paper_2101_01160_gb300 import mdlg
@@ -260,6 +307,9 @@ def run_profile_case(args):
     elif args.profile_case == "disp":
         r = _time_disp_hist(mdlg, torch, reps=3)
         print(json.dumps({"profile_case": "disp", **r}))
+    elif args.profile_case == "local":
+        r = _time_local_fields(mdlg, torch, reps=2)
+        print(json.dumps({"profile_case": "local", **r}))
     else:
         r = _time_surrogate(mdlg, torch, reps=3)
         print(json.dumps({"profile_case": "mlp", **r}))
@@ -354,6 +404,7 @@ def run_ours(args):
         variants["batched_fp32_over_plain_fp64"] = (value / ws) / variants["plain_fp64"]["value"]
         variants["surrogate_inference"] = _time_surrogate(mdlg, torch)
         variants["disp_hist"] = _time_disp_hist(mdlg, torch)
+        variants["local_fields"] = _time_local_fields(mdlg, torch)
 
     peak, peak_kind = _peaks()
     kern_avg_s = (sum(kern_ms) / len(kern_ms)) * 1e-3
@@ -451,7 +502,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-variants", action="store_true")
-    ap.add_argument("--profile-case", choices=["md64", "mlp", "disp"], default=None,
+    ap.add_argument("--profile-case", choices=["md64", "mlp", "disp", "local"], default=None,
                     help="run a small case for ncu captures instead of the bench")
     args = ap.parse_args()
     if args.profile_case:

@@ -110,27 +110,38 @@ __global__ void k_site_occupation(LocSnap a, LocSnap b, int n, OccParams P, int 
     }
 }
 
-// Grid (x tiles, row y, class i): one thread per entry (i, y, x) with
-// xi = n_next[i][(y + vy) mod lx][(x + vx) mod lx] - n_t[i][y][x]; the
-// class shift, reduced into [0, lx) once per block, needs one conditional
-// subtract per coordinate.
-__global__ void k_collision(const int *nt, const int *nn, int lx, int W, double scale, int *xi_out,
-                            double *omega_out) {
+// Grid (row tiles of `rows` rows, class i): each thread walks the tile's
+// entries (y, x) in steps of the block size, keeping (y, x) incrementally,
+// and writes xi = n_next[i][(y + vy) mod lx][(x + vx) mod lx] - n_t[i][y][x].
+// The class shift is reduced into [0, lx) once per thread, so the periodic
+// wrap is one conditional subtract per coordinate.
+__global__ void k_collision(const int *nt, const int *nn, int lx, int W, int rows, double scale,
+                            int *xi_out, double *omega_out) {
     const int side = 2 * W + 1;
-    const int i = blockIdx.z, y = blockIdx.y;
-    const int x = blockIdx.x * blockDim.x + threadIdx.x;
-    if (x >= lx) return;
+    const int i = blockIdx.y;
     int sx = (i % side - W) % lx, sy = (i / side - W) % lx;
     if (sx < 0) sx += lx;
     if (sy < 0) sy += lx;
-    int xd = x + sx, yd = y + sy;
-    if (xd >= lx) xd -= lx;
-    if (yd >= lx) yd -= lx;
+    const int y0 = blockIdx.x * rows;
+    const int y1 = min(lx, y0 + rows);
     const long long plane = (long long)i * lx * lx;
-    const long long e = plane + (long long)y * lx + x;
-    const int v = nn[plane + (long long)yd * lx + xd] - nt[e];
-    if (xi_out) xi_out[e] = v;
-    if (omega_out) omega_out[e] = scale * (double)v;
+    int y = y0 + (int)(threadIdx.x / lx), x = (int)(threadIdx.x % lx);
+    const int step_y = (int)(blockDim.x / lx), step_x = (int)(blockDim.x % lx);
+    while (y < y1) {
+        int xd = x + sx, yd = y + sy;
+        if (xd >= lx) xd -= lx;
+        if (yd >= lx) yd -= lx;
+        const long long e = plane + (long long)y * lx + x;
+        const int v = nn[plane + (long long)yd * lx + xd] - nt[e];
+        if (xi_out) xi_out[e] = v;
+        if (omega_out) omega_out[e] = scale * (double)v;
+        x += step_x;
+        y += step_y;
+        if (x >= lx) {
+            x -= lx;
+            ++y;
+        }
+    }
 }
 
 // One wave of resident CTAs (occupancy of the instantiation times the SM
@@ -213,8 +224,10 @@ extern "C" int mdlg_collision(const int32_t *n_t, const int32_t *n_next, int32_t
     const int64_t side = 2 * (int64_t)W + 1;
     const int64_t total = side * side * (int64_t)lx * lx;
     if (total >= (int64_t)1 << 31) return fail(MD_E_LIMIT, "mdlg_collision: (2W+1)^2 lx^2 must be < 2^31");
-    const dim3 grid((lx + 127) / 128, lx, (unsigned)(side * side));
-    k_collision<<<grid, 128, 0, (cudaStream_t)stream>>>(n_t, n_next, lx, W, scale, xi_out, omega_out);
+    // about 2048 entries (a few rows) per block
+    const int rows = lx >= 2048 ? 1 : 2048 / lx;
+    const dim3 grid((unsigned)((lx + rows - 1) / rows), (unsigned)(side * side));
+    k_collision<<<grid, 256, 0, (cudaStream_t)stream>>>(n_t, n_next, lx, W, rows, scale, xi_out, omega_out);
     MD_CUDA_TRY(cudaGetLastError());
     return MD_OK;
 }

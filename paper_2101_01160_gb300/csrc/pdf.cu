@@ -5,11 +5,12 @@
 // element-wise K(X_i) of Eq. k_Xi.
 //
 // The displacement is taken in the cell frame, wrap(c1 - c0) * h +
-// (off1 - off0) with the cell difference wrapped to the nearest image: one
-// rounding (none but the final sum for FP32 offsets) and a handful of FP64
-// operations, the limiting resource of this kernel on GB300 (its FP64 pipe
-// runs near saturation).  The bin is floor(delta * (1 / width)), every
-// operation rounded on its own, so bin indices are exact.  The histogram is privatised per CTA in shared memory
+// (off1 - off0) with the cell difference wrapped to the nearest image, and
+// its bin is floor(delta * (1 / width)), every operation of that FP64
+// definition rounded on its own.  The kernel decides the bin in FP32 with a
+// proven error bound and falls back to the FP64 definition only near bin
+// edges (GB300's FP64 rate is a small fraction of its FP32 rate), so bin
+// indices are exact.  The histogram is privatised per CTA in shared memory
 // and flushed with 64-bit atomics: integer counts do not depend on the
 // launch.
 #include <cmath>
@@ -28,9 +29,39 @@ struct PdfSnap {
     int f64;
 };
 
+// Bin index of one displacement component, floor(RN(d * inv_w)) with d =
+// RN(RN(dc * h) + RN(o1 - o0)) in FP64 (the definition), decided in FP32
+// wherever FP32 provably gives the same integer.  With a = RN32(dc * hf),
+// hf = RN32(h), invwf = RN32(inv_w):
+//     q = RN32(RN32(a + RN32(o1 - o0)) * invwf),
+//     S = RN32((|a| + |o1| + |o0|) * invwf),
+// q differs from (dc h + o1 - o0) inv_w by less than 0.875 S 2^-21 (two
+// roundings of dc h, one of the offset difference, one of the sum, two of
+// the product, one per offset if they are FP64 -- each at most 2^-24
+// relative to |a| + |o1| + |o0|), and the FP64 value by a few 2^-53 of the
+// same.  So when q is more than S 2^-20 from the nearest integer, floor(q)
+// is the bin; otherwise (values on or within about S 1e-6 of a bin edge) the
+// FP64 evaluation decides.  Bit-identical to the FP64 definition for finite
+// inputs.
 template <typename T>
-__global__ void k_disp_hist(PdfSnap a, PdfSnap b, int n, int ncell, double h, double inv_w, int nbins,
-                            unsigned long long *hist, unsigned long long *outside) {
+__device__ __forceinline__ long long disp_bin(int dc, T o1, T o0, double h, float hf, double inv_w,
+                                              float invwf) {
+    const float a = __fmul_rn((float)dc, hf);
+    const float f1 = (float)o1, f0 = (float)o0;
+    const float q = __fmul_rn(__fadd_rn(a, __fsub_rn(f1, f0)), invwf);
+    const float S = __fmul_rn(__fadd_rn(__fadd_rn(fabsf(a), fabsf(f1)), fabsf(f0)), invwf);
+    if (S < 0x1p22f && fabsf(__fsub_rn(q, rintf(q))) > __fmul_rn(S, 0x1p-20f))
+        return (long long)floorf(q);
+    const double doff = __dsub_rn((double)o1, (double)o0);
+    const double d = __dadd_rn(__dmul_rn((double)dc, h), doff);
+    // floor as an integer in one round-down conversion
+    return __double2ll_rd(__dmul_rn(d, inv_w));
+}
+
+template <typename T>
+__global__ void k_disp_hist(PdfSnap a, PdfSnap b, int n, int ncell, float inv_ncell, double h, float hf,
+                            double inv_w, float invwf, int nbins, unsigned long long *hist,
+                            unsigned long long *outside) {
     extern __shared__ unsigned int sh_bins[];
     for (int k = threadIdx.x; k < nbins; k += blockDim.x) sh_bins[k] = 0u;
     __syncthreads();
@@ -39,18 +70,15 @@ __global__ void k_disp_hist(PdfSnap a, PdfSnap b, int n, int ncell, double h, do
     const T *o0[2] = {static_cast<const T *>(a.ox), static_cast<const T *>(a.oy)};
     const T *o1[2] = {static_cast<const T *>(b.ox), static_cast<const T *>(b.oy)};
     for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < n; j += gridDim.x * blockDim.x) {
-        const int c0 = a.cell[j], c1 = b.cell[j];
-        const int cc0[2] = {c0 % ncell, c0 / ncell}, cc1[2] = {c1 % ncell, c1 / ncell};
+        int cc0[2], cc1[2];
+        split_cell(a.cell[j], ncell, inv_ncell, cc0[0], cc0[1]);
+        split_cell(b.cell[j], ncell, inv_ncell, cc1[0], cc1[1]);
 #pragma unroll
         for (int ax = 0; ax < 2; ++ax) {
             int dc = cc1[ax] - cc0[ax];
             if (dc > ncell / 2) dc -= ncell;
             if (dc < -(ncell / 2)) dc += ncell;
-            const double doff = __dsub_rn((double)o1[ax][j], (double)o0[ax][j]);
-            const double d = __dadd_rn(__dmul_rn((double)dc, h), doff);
-            // floor(d / width) as an integer in one conversion (round down;
-            // the range test is then integer, no FP64 floor or compare)
-            const long long k = __double2ll_rd(__dmul_rn(d, inv_w));
+            const long long k = disp_bin<T>(dc, o1[ax][j], o0[ax][j], h, hf, inv_w, invwf);
             if (k >= lo && k < hi)
                 atomicAdd(&sh_bins[(int)(k - lo)], 1u);
             else
@@ -127,14 +155,15 @@ extern "C" int mdlg_disp_hist(const md_snapshot *t0, const md_snapshot *t1, int6
     PdfSnap a{t0->cell, t0->off_x, t0->off_y, t0->off_is_f64};
     PdfSnap b{t1->cell, t1->off_x, t1->off_y, t1->off_is_f64};
     const double inv_w = 1.0 / width;
+    const float invwf = (float)inv_w, hf = (float)t0->h, inv_ncell = 1.0f / (float)t0->ncell;
     const size_t smem = sizeof(unsigned) * nbins;
     if (t0->off_is_f64)
-        k_disp_hist<double><<<pdf_grid(n), 256, smem, st>>>(a, b, (int)n, t0->ncell, t0->h, inv_w, nbins,
-                                                           (unsigned long long *)hist_out,
+        k_disp_hist<double><<<pdf_grid(n), 256, smem, st>>>(a, b, (int)n, t0->ncell, inv_ncell, t0->h, hf,
+                                                           inv_w, invwf, nbins, (unsigned long long *)hist_out,
                                                            (unsigned long long *)outside_out);
     else
-        k_disp_hist<float><<<pdf_grid(n), 256, smem, st>>>(a, b, (int)n, t0->ncell, t0->h, inv_w, nbins,
-                                                          (unsigned long long *)hist_out,
+        k_disp_hist<float><<<pdf_grid(n), 256, smem, st>>>(a, b, (int)n, t0->ncell, inv_ncell, t0->h, hf,
+                                                          inv_w, invwf, nbins, (unsigned long long *)hist_out,
                                                           (unsigned long long *)outside_out);
     MD_CUDA_TRY(cudaGetLastError());
     return MD_OK;
