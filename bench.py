@@ -285,7 +285,7 @@ def run_profile_case(args):
     surrogate forward passes on 1M queries; disp = eight displacement-PDF
     histograms of a 16.8M-particle snapshot pair; local = the occupation and
     collision kernels of the local fields on a 6.4M-particle ensemble snapshot
-    pair (five launches each after two occupation calls)."""
+    pair (two occupation calls, then three occupation + collision pairs)."""
     import torch
 
     from paper_2101_01160_gb300 import mdlg
@@ -308,8 +308,19 @@ def run_profile_case(args):
         r = _time_disp_hist(mdlg, torch, reps=3)
         print(json.dumps({"profile_case": "disp", **r}))
     elif args.profile_case == "local":
-        r = _time_local_fields(mdlg, torch, reps=2)
-        print(json.dumps({"profile_case": "local", **r}))
+        from paper_2101_01160_gb300 import inputs
+
+        n, ncell, lx, W = 64 * 99_856, 333, 250, 4
+        h = float(np.float32(1000.0 / ncell))
+        sn = inputs.random_celloff_snapshots(n, ncell, h, seed=77, max_step=4.0, lattice_dx=ncell * h / lx)
+        d = [torch.from_numpy(sn[k]).cuda() for k in ("cell0", "ox0", "oy0", "cell1", "ox1", "oy1")]
+        field, ovf = mdlg.site_occupation(*d, ncell, h, lx, W)
+        f2, _ = mdlg.site_occupation(*d, ncell, h, lx, W)
+        for _ in range(3):
+            mdlg.site_occupation(*d, ncell, h, lx, W, field=field, ovf=ovf)
+            mdlg.collision(field, f2, W)
+        torch.cuda.synchronize()
+        print(json.dumps({"profile_case": "local", "particles": n, "field_entries": int(field.numel())}))
     else:
         r = _time_surrogate(mdlg, torch, reps=3)
         print(json.dumps({"profile_case": "mlp", **r}))

@@ -64,6 +64,12 @@ __device__ __forceinline__ long long lattice_cell_mul(double x, double dxl, doub
 // for every finite encoded position; in the common case a few FP32 and
 // 32-bit integer operations replace the FP64 ones and the 64-bit modulo
 // (GB300's FP64 rate is a small fraction of its FP32 rate).  lx < 2^22.
+// The FP64 evaluation, out of line: it runs only near lattice lines, and
+// keeping it out of the unrolled callers keeps their code small.
+static __device__ __noinline__ int lattice_cell_slow(int c, double off, double h, double dxl, int lx) {
+    return (int)lattice_cell(cell_position(c, h, off), dxl, lx);
+}
+
 template <typename T>
 __device__ __forceinline__ int lattice_cell_f32(int c, T off, double h, float hf, double dxl, float invf,
                                                 int lx) {
@@ -83,7 +89,7 @@ __device__ __forceinline__ int lattice_cell_f32(int c, T off, double h, float hf
         }
         return l;
     }
-    return (int)lattice_cell(cell_position(c, h, (double)off), dxl, lx);
+    return lattice_cell_slow(c, (double)off, h, dxl, lx);
 }
 
 // Splits a linear cell index c = cy * ncell + cx (0 <= cx, cy < ncell,

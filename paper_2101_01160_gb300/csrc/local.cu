@@ -127,20 +127,43 @@ __global__ void k_collision(const int *nt, const int *nn, int lx, int W, int row
     const long long plane = (long long)i * lx * lx;
     int y = y0 + (int)(threadIdx.x / lx), x = (int)(threadIdx.x % lx);
     const int step_y = (int)(blockDim.x / lx), step_x = (int)(blockDim.x % lx);
-    while (y < y1) {
-        int xd = x + sx, yd = y + sy;
+    auto advance = [&](int &ax, int &ay) {
+        ax += step_x;
+        ay += step_y;
+        if (ax >= lx) {
+            ax -= lx;
+            ++ay;
+        }
+    };
+    auto source = [&](int ax, int ay) {
+        int xd = ax + sx, yd = ay + sy;
         if (xd >= lx) xd -= lx;
         if (yd >= lx) yd -= lx;
-        const long long e = plane + (long long)y * lx + x;
-        const int v = nn[plane + (long long)yd * lx + xd] - nt[e];
-        if (xi_out) xi_out[e] = v;
-        if (omega_out) omega_out[e] = scale * (double)v;
-        x += step_x;
-        y += step_y;
-        if (x >= lx) {
-            x -= lx;
-            ++y;
+        return plane + (long long)yd * lx + xd;
+    };
+    // two entries per iteration, their four loads issued together
+    while (y < y1) {
+        int x2 = x, y2 = y;
+        advance(x2, y2);
+        const bool two = y2 < y1;
+        const long long e1 = plane + (long long)y * lx + x;
+        const long long e2 = plane + (long long)y2 * lx + x2;
+        const int a1 = nn[source(x, y)], b1 = nt[e1];
+        int a2 = 0, b2 = 0;
+        if (two) {
+            a2 = nn[source(x2, y2)];
+            b2 = nt[e2];
         }
+        const int v1 = a1 - b1, v2 = a2 - b2;
+        if (xi_out) xi_out[e1] = v1;
+        if (omega_out) omega_out[e1] = scale * (double)v1;
+        if (two) {
+            if (xi_out) xi_out[e2] = v2;
+            if (omega_out) omega_out[e2] = scale * (double)v2;
+        }
+        x = x2;
+        y = y2;
+        advance(x, y);
     }
 }
 

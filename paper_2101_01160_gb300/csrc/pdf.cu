@@ -43,6 +43,14 @@ struct PdfSnap {
 // is the bin; otherwise (values on or within about S 1e-6 of a bin edge) the
 // FP64 evaluation decides.  Bit-identical to the FP64 definition for finite
 // inputs.
+// The FP64 definition, out of line (it runs only near bin edges).
+__device__ __noinline__ long long disp_bin_slow(int dc, double o1, double o0, double h, double inv_w) {
+    const double doff = __dsub_rn(o1, o0);
+    const double d = __dadd_rn(__dmul_rn((double)dc, h), doff);
+    // floor as an integer in one round-down conversion
+    return __double2ll_rd(__dmul_rn(d, inv_w));
+}
+
 template <typename T>
 __device__ __forceinline__ long long disp_bin(int dc, T o1, T o0, double h, float hf, double inv_w,
                                               float invwf) {
@@ -52,10 +60,7 @@ __device__ __forceinline__ long long disp_bin(int dc, T o1, T o0, double h, floa
     const float S = __fmul_rn(__fadd_rn(__fadd_rn(fabsf(a), fabsf(f1)), fabsf(f0)), invwf);
     if (S < 0x1p22f && fabsf(__fsub_rn(q, rintf(q))) > __fmul_rn(S, 0x1p-20f))
         return (long long)floorf(q);
-    const double doff = __dsub_rn((double)o1, (double)o0);
-    const double d = __dadd_rn(__dmul_rn((double)dc, h), doff);
-    // floor as an integer in one round-down conversion
-    return __double2ll_rd(__dmul_rn(d, inv_w));
+    return disp_bin_slow(dc, (double)o1, (double)o0, h, inv_w);
 }
 
 template <typename T>
