@@ -78,7 +78,7 @@ __device__ __forceinline__ int lattice_cell_f32(int c, T off, double h, float hf
     const float q = __fmul_rn(__fadd_rn(a, o), invf);
     const float S = __fmul_rn(__fadd_rn(fabsf(a), fabsf(o)), invf);
     if (S < 0x1p22f && fabsf(__fsub_rn(q, rintf(q))) > __fmul_rn(S, 0x1p-20f)) {
-        int l = (int)floorf(q);
+        int l = __float2int_rd(q);   // |q| < 2^22: floor in one 32-bit conversion
         // positions within a box edge of the box need one wrap; others the
         // general reduction
         if (l < 0) l += lx;

@@ -58,42 +58,89 @@ __device__ __forceinline__ long long disp_bin(int dc, T o1, T o0, double h, floa
     const float f1 = (float)o1, f0 = (float)o0;
     const float q = __fmul_rn(__fadd_rn(a, __fsub_rn(f1, f0)), invwf);
     const float S = __fmul_rn(__fadd_rn(__fadd_rn(fabsf(a), fabsf(f1)), fabsf(f0)), invwf);
+    // |q| < 2^22 here: a 32-bit round-down conversion (a 64-bit one would
+    // run on the FP64 pipe)
     if (S < 0x1p22f && fabsf(__fsub_rn(q, rintf(q))) > __fmul_rn(S, 0x1p-20f))
-        return (long long)floorf(q);
+        return __float2int_rd(q);
     return disp_bin_slow(dc, (double)o1, (double)o0, h, inv_w);
 }
 
+template <typename T> struct PdfVec4;
+template <> struct PdfVec4<float> {
+    static __device__ __forceinline__ void load(const float *p, float (&v)[4]) {
+        const float4 q = __ldg(reinterpret_cast<const float4 *>(p));
+        v[0] = q.x; v[1] = q.y; v[2] = q.z; v[3] = q.w;
+    }
+};
+template <> struct PdfVec4<double> {
+    static __device__ __forceinline__ void load(const double *p, double (&v)[4]) {
+        const double2 q0 = __ldg(reinterpret_cast<const double2 *>(p));
+        const double2 q1 = __ldg(reinterpret_cast<const double2 *>(p) + 1);
+        v[0] = q0.x; v[1] = q0.y; v[2] = q1.x; v[3] = q1.y;
+    }
+};
+
+struct DispParams {
+    int ncell, nbins;
+    float inv_ncell, hf, invwf;
+    double h, inv_w;
+};
+
+// Counts both displacement components of one particle into the CTA's bins.
 template <typename T>
-__global__ void k_disp_hist(PdfSnap a, PdfSnap b, int n, int ncell, float inv_ncell, double h, float hf,
-                            double inv_w, float invwf, int nbins, unsigned long long *hist,
+__device__ __forceinline__ void disp_count(const DispParams &P, int c0, int c1, T x0, T y0, T x1, T y1,
+                                           unsigned *sh_bins, unsigned &my_out) {
+    int cc0[2], cc1[2];
+    split_cell(c0, P.ncell, P.inv_ncell, cc0[0], cc0[1]);
+    split_cell(c1, P.ncell, P.inv_ncell, cc1[0], cc1[1]);
+    const T o0[2] = {x0, y0}, o1[2] = {x1, y1};
+    const long long lo = -(long long)(P.nbins / 2), hi = (long long)P.nbins - P.nbins / 2;
+#pragma unroll
+    for (int ax = 0; ax < 2; ++ax) {
+        int dc = cc1[ax] - cc0[ax];
+        if (dc > P.ncell / 2) dc -= P.ncell;
+        if (dc < -(P.ncell / 2)) dc += P.ncell;
+        const long long k = disp_bin<T>(dc, o1[ax], o0[ax], P.h, P.hf, P.inv_w, P.invwf);
+        if (k >= lo && k < hi)
+            atomicAdd(&sh_bins[(int)(k - lo)], 1u);
+        else
+            ++my_out;
+    }
+}
+
+// Grid-stride over groups of four consecutive particles (VEC: 16-byte
+// aligned arrays read with vector loads, all loads of a group issued before
+// any arithmetic), then the last n % 4 particles one per thread.
+template <typename T, bool VEC>
+__global__ void k_disp_hist(PdfSnap a, PdfSnap b, int n, DispParams P, unsigned long long *hist,
                             unsigned long long *outside) {
     extern __shared__ unsigned int sh_bins[];
-    for (int k = threadIdx.x; k < nbins; k += blockDim.x) sh_bins[k] = 0u;
+    for (int k = threadIdx.x; k < P.nbins; k += blockDim.x) sh_bins[k] = 0u;
     __syncthreads();
     unsigned my_out = 0;
-    const long long lo = -(long long)(nbins / 2), hi = (long long)nbins - nbins / 2;
-    const T *o0[2] = {static_cast<const T *>(a.ox), static_cast<const T *>(a.oy)};
-    const T *o1[2] = {static_cast<const T *>(b.ox), static_cast<const T *>(b.oy)};
-    for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < n; j += gridDim.x * blockDim.x) {
-        int cc0[2], cc1[2];
-        split_cell(a.cell[j], ncell, inv_ncell, cc0[0], cc0[1]);
-        split_cell(b.cell[j], ncell, inv_ncell, cc1[0], cc1[1]);
+    const T *ax = static_cast<const T *>(a.ox), *ay = static_cast<const T *>(a.oy);
+    const T *bx = static_cast<const T *>(b.ox), *by = static_cast<const T *>(b.oy);
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    const long long tid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const long long ngroup = VEC ? n / 4 : 0;
+    for (long long g = tid; g < ngroup; g += stride) {
+        const int4 q0 = __ldg(reinterpret_cast<const int4 *>(a.cell) + g);
+        const int4 q1 = __ldg(reinterpret_cast<const int4 *>(b.cell) + g);
+        const int c0[4] = {q0.x, q0.y, q0.z, q0.w}, c1[4] = {q1.x, q1.y, q1.z, q1.w};
+        T x0[4], y0[4], x1[4], y1[4];
+        PdfVec4<T>::load(ax + 4 * g, x0);
+        PdfVec4<T>::load(ay + 4 * g, y0);
+        PdfVec4<T>::load(bx + 4 * g, x1);
+        PdfVec4<T>::load(by + 4 * g, y1);
 #pragma unroll
-        for (int ax = 0; ax < 2; ++ax) {
-            int dc = cc1[ax] - cc0[ax];
-            if (dc > ncell / 2) dc -= ncell;
-            if (dc < -(ncell / 2)) dc += ncell;
-            const long long k = disp_bin<T>(dc, o1[ax][j], o0[ax][j], h, hf, inv_w, invwf);
-            if (k >= lo && k < hi)
-                atomicAdd(&sh_bins[(int)(k - lo)], 1u);
-            else
-                ++my_out;
-        }
+        for (int u = 0; u < 4; ++u) disp_count<T>(P, c0[u], c1[u], x0[u], y0[u], x1[u], y1[u], sh_bins, my_out);
     }
+    for (long long j = 4 * ngroup + tid; j < n; j += stride)
+        disp_count<T>(P, a.cell[j], b.cell[j], ax[j], ay[j], bx[j], by[j], sh_bins, my_out);
     for (int o = 16; o > 0; o >>= 1) my_out += __shfl_xor_sync(0xffffffffu, my_out, o);
     if ((threadIdx.x & 31) == 0 && my_out) atomicAdd(outside, (unsigned long long)my_out);
     __syncthreads();
-    for (int k = threadIdx.x; k < nbins; k += blockDim.x)
+    for (int k = threadIdx.x; k < P.nbins; k += blockDim.x)
         if (sh_bins[k]) atomicAdd(&hist[k], (unsigned long long)sh_bins[k]);
 }
 
@@ -123,16 +170,17 @@ __global__ void k_kl_terms(const double *R, const double *Q, int n, double *K) {
     if (i < n) K[i] = R[i] > 0.0 ? R[i] * log(R[i] / Q[i]) : 0.0;
 }
 
-int pdf_grid(int64_t n) {
-    static int nsm = 0;
-    if (nsm == 0) {
-        int dev = 0;
-        cudaGetDevice(&dev);
-        cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-        if (nsm <= 0) nsm = 1;
-    }
-    int64_t g = (n + 255) / 256;
-    if (g > (int64_t)nsm * 8) g = (int64_t)nsm * 8;
+// One wave of resident CTAs of the histogram kernel (its occupancy with
+// `smem` bytes of bins times the SM count), fewer when there is less work.
+template <typename K>
+int disp_grid(K kernel, long long work, size_t smem) {
+    int dev = 0, nsm = 1, per_sm = 1;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, 256, smem);
+    long long g = (long long)(nsm > 0 ? nsm : 1) * (per_sm > 0 ? per_sm : 1);
+    const long long need = (work + 255) / 256;
+    if (need < g) g = need;
     return (int)(g < 1 ? 1 : g);
 }
 
@@ -159,17 +207,29 @@ extern "C" int mdlg_disp_hist(const md_snapshot *t0, const md_snapshot *t1, int6
     if (n == 0) return MD_OK;
     PdfSnap a{t0->cell, t0->off_x, t0->off_y, t0->off_is_f64};
     PdfSnap b{t1->cell, t1->off_x, t1->off_y, t1->off_is_f64};
-    const double inv_w = 1.0 / width;
-    const float invwf = (float)inv_w, hf = (float)t0->h, inv_ncell = 1.0f / (float)t0->ncell;
+    DispParams P;
+    P.ncell = t0->ncell;
+    P.nbins = nbins;
+    P.h = t0->h;
+    P.inv_w = 1.0 / width;
+    P.hf = (float)t0->h;
+    P.invwf = (float)P.inv_w;
+    P.inv_ncell = 1.0f / (float)t0->ncell;
     const size_t smem = sizeof(unsigned) * nbins;
-    if (t0->off_is_f64)
-        k_disp_hist<double><<<pdf_grid(n), 256, smem, st>>>(a, b, (int)n, t0->ncell, inv_ncell, t0->h, hf,
-                                                           inv_w, invwf, nbins, (unsigned long long *)hist_out,
-                                                           (unsigned long long *)outside_out);
-    else
-        k_disp_hist<float><<<pdf_grid(n), 256, smem, st>>>(a, b, (int)n, t0->ncell, inv_ncell, t0->h, hf,
-                                                          inv_w, invwf, nbins, (unsigned long long *)hist_out,
-                                                          (unsigned long long *)outside_out);
+    auto al16 = [](const void *p) { return ((uintptr_t)p & 15u) == 0; };
+    const bool vec = al16(a.cell) && al16(a.ox) && al16(a.oy) && al16(b.cell) && al16(b.ox) && al16(b.oy);
+    unsigned long long *h64 = (unsigned long long *)hist_out, *o64 = (unsigned long long *)outside_out;
+    const long long work = vec ? (n + 3) / 4 : n;
+    auto go = [&](auto kernel) {
+        kernel<<<disp_grid(kernel, work, smem), 256, smem, st>>>(a, b, (int)n, P, h64, o64);
+    };
+    if (t0->off_is_f64) {
+        if (vec) go(k_disp_hist<double, true>);
+        else go(k_disp_hist<double, false>);
+    } else {
+        if (vec) go(k_disp_hist<float, true>);
+        else go(k_disp_hist<float, false>);
+    }
     MD_CUDA_TRY(cudaGetLastError());
     return MD_OK;
 }
