@@ -170,7 +170,7 @@ def _time_variant(mdlg, torch, params, st, md_steps, reps=3):
     return {"value": params.n * md_steps / (m * 1e-3), "ms_per_launch": m, "md_steps": md_steps}
 
 
-def _time_surrogate(mdlg, torch, n=1 << 20, reps=5):
+def _time_surrogate(mdlg, torch, n=1 << 20, reps=20):
     """Fused f_eq-surrogate forward pass (4 -> 256 x4 SiLU -> 81 softmax,
     BF16 tensor cores) on n query points; random-initialised weights of the
     trained architecture (the flop count does not depend on the values)."""
@@ -180,19 +180,8 @@ def _time_surrogate(mdlg, torch, n=1 << 20, reps=5):
     X = torch.from_numpy(inputs.surrogate_queries(n, 3, lo=(0.02, 1.0, 0.05, 1.0),
                                                   hi=(0.30, 20.0, 0.2, 4.0))).cuda()
     out = torch.empty((n, model.n_classes), dtype=torch.float32, device="cuda")
-    for _ in range(3):
-        model.forward(X, out=out)
-    torch.cuda.synchronize()
-    ms = []
-    for _ in range(reps):
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record()
-        model.forward(X, out=out)
-        e1.record()
-        torch.cuda.synchronize()
-        ms.append(e0.elapsed_time(e1))
+    m = _time_queued(torch, lambda: model.forward(X, out=out), reps)
     model.status()
-    m = float(np.median(ms))
     sizes = mdlg.SURR_SIZES
     flop = 2.0 * sum(a * b for a, b in zip(sizes[:-1], sizes[1:])) * n
     peak, kind = _peaks("bf16_tflops", 1900.0)
@@ -202,7 +191,34 @@ def _time_surrogate(mdlg, torch, n=1 << 20, reps=5):
             "kernel": "k_mlp_fused", "workload": "1,048,576 queries uniform in the training box"}
 
 
-def _time_disp_hist(mdlg, torch, n=1 << 24, reps=5):
+def _time_queued(torch, fn, reps=20):
+    """Device time of one launch of fn with a cold L2: reps x (256 MB L2
+    flush + fn) queued back to back between two CUDA events, less reps
+    flushes alone, over reps.  The queue keeps the GPU ahead of the host, so
+    the host's call overhead is not counted."""
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+
+    def span(with_fn):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record()
+        for _ in range(reps):
+            flush.zero_()
+            if with_fn:
+                fn()
+        e1.record()
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1)
+
+    for _ in range(3):
+        fn()
+    span(True)
+    both = min(span(True) for _ in range(3))
+    alone = min(span(False) for _ in range(3))
+    return max(both - alone, 0.0) / reps
+
+
+def _time_disp_hist(mdlg, torch, n=1 << 24, reps=20):
     """Displacement-PDF histogram (Sec. 3(b), Fig. 2) of a synthetic FP32
     snapshot pair of n particles (400 MB, above L2); algorithmic traffic
     24 B per particle (two snapshots of cell + two FP32 offsets)."""
@@ -212,18 +228,7 @@ def _time_disp_hist(mdlg, torch, n=1 << 24, reps=5):
     h = float(np.float32(6482.12 / ncell))
     s = inputs.random_celloff_snapshots(n, ncell, h, seed=5, max_step=6.0)
     arrs = [torch.from_numpy(s[k]).cuda() for k in ("cell0", "ox0", "oy0", "cell1", "ox1", "oy1")]
-    for _ in range(3):
-        mdlg.disp_hist(*arrs, ncell, h, 0.05, 512)
-    torch.cuda.synchronize()
-    ms = []
-    for _ in range(reps):
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record()
-        mdlg.disp_hist(*arrs, ncell, h, 0.05, 512)
-        e1.record()
-        torch.cuda.synchronize()
-        ms.append(e0.elapsed_time(e1))
-    m = float(np.median(ms))
+    m = _time_queued(torch, lambda: mdlg.disp_hist(*arrs, ncell, h, 0.05, 512), reps)
     peak, kind = _peaks()
     gbs = 24.0 * n / (m * 1e-3) / 1e9
     return {"particles": n, "ms_per_launch": m, "gbs": gbs, "peak_gbs": peak, "peak_kind": kind,
@@ -231,14 +236,14 @@ def _time_disp_hist(mdlg, torch, n=1 << 24, reps=5):
             "workload": "synthetic FP32 snapshot pair, 16.8M particles, 512 bins of 0.05 sigma"}
 
 
-def _time_local_fields(mdlg, torch, reps=10):
+def _time_local_fields(mdlg, torch, reps=20):
     """Local MDLG fields (Sec. 2, Eqs. n_i and mdlg_evolution) of a synthetic
     ensemble snapshot pair: 64 replicas of the standard system's box (N =
-    99,856, L = 1000) in one call, on Table 1's lx = 250 lattice, W = 4.  L2
-    is flushed before every timed launch.  Algorithmic traffic: 24 B per
+    99,856, L = 1000) in one call, on Table 1's lx = 250 lattice, W = 4.
+    Algorithmic traffic: 24 B per
     particle for the occupation numbers (two FP32 snapshots; the 20 MB field
     stays in L2), 12 B per field entry for the collision operator (two int32
-    fields read, one written)."""
+    fields read, one written).  L2 is flushed before every launch."""
     from paper_2101_01160_gb300 import inputs
 
     n, ncell, lx, W = 64 * 99_856, 333, 250, 4
@@ -247,22 +252,14 @@ def _time_local_fields(mdlg, torch, reps=10):
     d = [torch.from_numpy(s[k]).cuda() for k in ("cell0", "ox0", "oy0", "cell1", "ox1", "oy1")]
     field, ovf = mdlg.site_occupation(*d, ncell, h, lx, W)
     f2, _ = mdlg.site_occupation(*d, ncell, h, lx, W)
-    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
-    out = {}
-    for name, fn in (("occupation", lambda: mdlg.site_occupation(*d, ncell, h, lx, W, field=field, ovf=ovf)),
-                     ("collision", lambda: mdlg.collision(field, f2, W))):
-        for _ in range(3):
-            fn()
-        ms = []
-        for _ in range(reps):
-            flush.zero_()
-            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            e0.record()
-            fn()
-            e1.record()
-            torch.cuda.synchronize()
-            ms.append(e0.elapsed_time(e1))
-        out[name] = float(np.median(ms))
+    xi = torch.empty_like(field)
+    lib = mdlg.load()
+    out = {
+        "occupation": _time_queued(torch, lambda: mdlg.site_occupation(*d, ncell, h, lx, W, field=field, ovf=ovf), reps),
+        # the C entry point directly, writing into a preallocated Xi field
+        "collision": _time_queued(torch, lambda: lib.mdlg_collision(mdlg._ptr(field), mdlg._ptr(f2), lx, W, 1.0,
+                                                                    mdlg._ptr(xi), None, None), reps),
+    }
     peak, kind = _peaks()
     entries = (2 * W + 1) ** 2 * lx * lx
     g_occ = 24.0 * n / (out["occupation"] * 1e-3) / 1e9
