@@ -300,22 +300,54 @@ def feq_batch(system, lg=0, dxi=0, symmetrize=True, out=None):
     return buf[:, :nb], buf[:, nb:2 * nb], buf[:, 2 * nb:3 * nb], buf[:, 3 * nb:]
 
 
+def _snapshots(cell0, ox0, oy0, cell1, ox1, oy1, ncell, h):
+    """Checks a snapshot pair (the C ABI sees only pointers and one length)
+    and returns (md_snapshot t0, md_snapshot t1, n): int32 cells and FP32 or
+    FP64 offsets of one dtype, all 1-D, contiguous, of equal length, on the
+    GPU.  Raises ValueError before any library call."""
+    import torch
+
+    arrs = (cell0, ox0, oy0, cell1, ox1, oy1)
+    if not all(isinstance(a, torch.Tensor) for a in arrs):
+        raise ValueError("snapshot arrays must be torch tensors")
+    n = cell0.numel()
+    if any(a.dim() != 1 or a.numel() != n or not a.is_contiguous() for a in arrs):
+        raise ValueError("snapshot arrays must be contiguous 1-D tensors of one length")
+    if cell0.dtype != torch.int32 or cell1.dtype != torch.int32:
+        raise ValueError("snapshot cells must be int32")
+    if ox0.dtype not in (torch.float32, torch.float64) or any(a.dtype != ox0.dtype for a in (oy0, ox1, oy1)):
+        raise ValueError("snapshot offsets must all be float32 or all float64")
+    if any(a.device.type != "cuda" for a in arrs) or len({a.device for a in arrs}) != 1:
+        raise ValueError("snapshot arrays must be on one CUDA device")
+    f64 = int(ox0.dtype == torch.float64)
+    s0 = md_snapshot(_ptr(cell0).value, _ptr(ox0).value, _ptr(oy0).value, f64, int(ncell), float(h))
+    s1 = md_snapshot(_ptr(cell1).value, _ptr(ox1).value, _ptr(oy1).value, f64, int(ncell), float(h))
+    return s0, s1, n
+
+
+def _field(t, shape, name, device):
+    import torch
+
+    if not isinstance(t, torch.Tensor) or t.dtype != torch.int32 or tuple(t.shape) != tuple(shape) \
+            or not t.is_contiguous() or t.device != device:
+        raise ValueError(f"{name} must be a contiguous int32 tensor of shape {tuple(shape)} on {device}")
+    return t
+
+
 def mdlg_bin(cell0, ox0, oy0, cell1, ox1, oy1, ncell, h, lx, W, stream=None, noalloc=False):
     """Histogram of lattice displacements between two device snapshots.
     noalloc=True calls mdlg_bin_noalloc (library-owned scratch; the outputs
     are still allocated here by torch)."""
     import torch
 
-    f64 = int(ox0.dtype == torch.float64)
-    s0 = md_snapshot(_ptr(cell0).value, _ptr(ox0).value, _ptr(oy0).value, f64, ncell, h)
-    s1 = md_snapshot(_ptr(cell1).value, _ptr(ox1).value, _ptr(oy1).value, f64, ncell, h)
+    s0, s1, n = _snapshots(cell0, ox0, oy0, cell1, ox1, oy1, ncell, h)
+    dev = cell0.device
     nb = (2 * W + 1) ** 2
-    hist = torch.empty(nb, dtype=torch.int32, device="cuda")
-    ovf = torch.empty(1, dtype=torch.int64, device="cuda")
-    mom = torch.empty(2, dtype=torch.float64, device="cuda")
+    hist = torch.empty(nb, dtype=torch.int32, device=dev)
+    ovf = torch.empty(1, dtype=torch.int64, device=dev)
+    mom = torch.empty(2, dtype=torch.float64, device=dev)
     fn = load().mdlg_bin_noalloc if noalloc else load().mdlg_bin
-    _check(fn(C.byref(s0), C.byref(s1), cell0.numel(), lx, W, _ptr(hist), _ptr(ovf), _ptr(mom),
-              _stream(stream)))
+    _check(fn(C.byref(s0), C.byref(s1), n, lx, W, _ptr(hist), _ptr(ovf), _ptr(mom), _stream(stream)))
     return hist, ovf, mom
 
 
@@ -324,12 +356,10 @@ def disp_hist(cell0, ox0, oy0, cell1, ox1, oy1, ncell, h, width, nbins, stream=N
     snapshots (Sec. 3(b), Fig. 2): (int64 tensor [nbins], outside count tensor)."""
     import torch
 
-    f64 = int(ox0.dtype == torch.float64)
-    s0 = md_snapshot(_ptr(cell0).value, _ptr(ox0).value, _ptr(oy0).value, f64, ncell, h)
-    s1 = md_snapshot(_ptr(cell1).value, _ptr(ox1).value, _ptr(oy1).value, f64, ncell, h)
-    hist = torch.empty(nbins, dtype=torch.int64, device="cuda")
-    out = torch.empty(1, dtype=torch.int64, device="cuda")
-    _check(load().mdlg_disp_hist(C.byref(s0), C.byref(s1), cell0.numel(), float(width), int(nbins),
+    s0, s1, n = _snapshots(cell0, ox0, oy0, cell1, ox1, oy1, ncell, h)
+    hist = torch.empty(int(nbins), dtype=torch.int64, device=cell0.device)
+    out = torch.empty(1, dtype=torch.int64, device=cell0.device)
+    _check(load().mdlg_disp_hist(C.byref(s0), C.byref(s1), n, float(width), int(nbins),
                                  _ptr(hist), _ptr(out), _stream(stream)))
     return hist, out
 
@@ -342,16 +372,20 @@ def site_occupation(cell0, ox0, oy0, cell1, ox1, oy1, ncell, h, lx, W, field=Non
     otherwise zeroed ones are made."""
     import torch
 
-    f64 = int(ox0.dtype == torch.float64)
-    s0 = md_snapshot(_ptr(cell0).value, _ptr(ox0).value, _ptr(oy0).value, f64, ncell, h)
-    s1 = md_snapshot(_ptr(cell1).value, _ptr(ox1).value, _ptr(oy1).value, f64, ncell, h)
+    lx, W = int(lx), int(W)
+    if lx < 1 or not 0 <= W <= MD_MAX_W:
+        raise ValueError("site_occupation: lx >= 1 and 0 <= W <= MD_MAX_W")
     q = (2 * W + 1) ** 2
-    if field is None:
-        field = torch.zeros((q, lx, lx), dtype=torch.int32, device="cuda")
-    if ovf is None:
-        ovf = torch.zeros((lx, lx), dtype=torch.int32, device="cuda")
-    _check(load().mdlg_site_occupation(C.byref(s0), C.byref(s1), cell0.numel(), int(lx), int(W),
-                                       _ptr(field), _ptr(ovf), _stream(stream)))
+    if q * lx * lx >= 1 << 31:
+        raise ValueError("site_occupation: (2W+1)^2 lx^2 must be < 2^31")
+    s0, s1, n = _snapshots(cell0, ox0, oy0, cell1, ox1, oy1, ncell, h)
+    dev = cell0.device
+    field = torch.zeros((q, lx, lx), dtype=torch.int32, device=dev) if field is None else \
+        _field(field, (q, lx, lx), "field", dev)
+    ovf = torch.zeros((lx, lx), dtype=torch.int32, device=dev) if ovf is None else \
+        _field(ovf, (lx, lx), "ovf", dev)
+    _check(load().mdlg_site_occupation(C.byref(s0), C.byref(s1), n, lx, W, _ptr(field), _ptr(ovf),
+                                       _stream(stream)))
     return field, ovf
 
 
@@ -361,7 +395,17 @@ def collision(n_t, n_next, W, scale=None, stream=None):
     ensemble-averaged Omega for fields summed over 1/scale replicas)."""
     import torch
 
+    W = int(W)
+    if not 0 <= W <= MD_MAX_W:
+        raise ValueError("collision: 0 <= W <= MD_MAX_W")
+    if not isinstance(n_t, torch.Tensor) or n_t.dim() != 3:
+        raise ValueError("collision: n_t must be a [(2W+1)^2, lx, lx] int32 tensor")
     lx = n_t.shape[-1]
+    shape = ((2 * W + 1) ** 2, lx, lx)
+    _field(n_t, shape, "n_t", n_t.device)
+    _field(n_next, shape, "n_next", n_t.device)
+    if n_t.device.type != "cuda":
+        raise ValueError("collision: fields must be on a CUDA device")
     if scale is None:
         out = torch.empty_like(n_t)
         _check(load().mdlg_collision(_ptr(n_t), _ptr(n_next), int(lx), int(W), 1.0, _ptr(out), None,

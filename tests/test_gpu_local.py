@@ -141,15 +141,29 @@ def test_lattice_line_neighbours_bitexact(mdlg, orc, lx):
 
 
 def test_rejects_bad_arguments(mdlg):
+    import ctypes as C
+
     z = torch.zeros(8, dtype=torch.int32, device="cuda")
     f = torch.zeros(8, dtype=torch.float32, device="cuda")
-    # every call is refused before a launch; the given outputs are never touched
+    # the binding refuses before any call ...
     for lx, W in ((0, 1), (4, 11), (20_000, 10)):                   # lx < 1, W > MD_MAX_W, too large
-        with pytest.raises(mdlg.MDError):
-            mdlg.site_occupation(z, f, f, z, f, f, 2, 1.0, lx, W, field=z, ovf=z)
+        with pytest.raises(ValueError):
+            mdlg.site_occupation(z, f, f, z, f, f, 2, 1.0, lx, W)
+    with pytest.raises(ValueError):                                  # field of the wrong shape
+        mdlg.site_occupation(z, f, f, z, f, f, 2, 1.0, 4, 1, field=z)
     n = torch.zeros((9, 3, 3), dtype=torch.int32, device="cuda")
-    with pytest.raises(mdlg.MDError):
+    with pytest.raises(ValueError):
         mdlg.collision(n, n, 11)
+    with pytest.raises(ValueError):                                  # W does not match the class count
+        mdlg.collision(n, n, 2)
+    # ... and so does the C ABI itself, before a launch (the outputs are never touched)
+    lib = mdlg.load()
+    s0 = mdlg.md_snapshot(z.data_ptr(), f.data_ptr(), f.data_ptr(), 0, 2, 1.0)
+    for lx, W, code in ((0, 1, mdlg.MD_E_ARG), (4, 11, mdlg.MD_E_ARG), (20_000, 10, mdlg.MD_E_LIMIT)):
+        rc = lib.mdlg_site_occupation(C.byref(s0), C.byref(s0), 8, lx, W, mdlg._ptr(z), mdlg._ptr(z), None)
+        assert rc == code, (lx, W, rc)
+    assert lib.mdlg_collision(mdlg._ptr(n), mdlg._ptr(n), 3, 11, 1.0, mdlg._ptr(n), None, None) == mdlg.MD_E_ARG
+    assert lib.mdlg_collision(mdlg._ptr(n), mdlg._ptr(n), 3, 1, 1.0, None, None, None) == mdlg.MD_E_ARG
     torch.cuda.synchronize()
 
 
