@@ -437,7 +437,9 @@ def run_ours(args):
                      "peak_kind": peak_kind,
                      "bytes_per_particle_step": BYTES_PER_PARTICLE_STEP},
         "e2e": e2e,
-        "gpu_launches": args.steps * 2,
+        # per step: the persistent MD launch and the f_eq stage's three
+        # (moments and lambda, WSG terms split over CTAs, the rest)
+        "gpu_launches": args.steps * 4,
         "clocks": clk.summary(),
         "f_eq_err": feq_err,
         "variants": variants,

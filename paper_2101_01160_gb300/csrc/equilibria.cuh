@@ -22,6 +22,27 @@ __device__ inline double cell_gauss_1d(double u, double var) {
     return norm * e + 0.5 * um * (erf(um / s) - eu) + 0.5 * up * (erf(up / s) - eu);
 }
 
+// cell_gauss_1d(v, var) for the 2W+1 displacements v = -W..W into out[0..2W]
+// (W <= 10).  Neighbouring v share two of their three points u-1, u, u+1, so
+// the exponentials and error functions are evaluated once at each of the
+// 2W+3 points -W-1..W+1 and combined with the arithmetic of cell_gauss_1d.
+__device__ inline void cell_gauss_row(double var, int W, double *out) {
+    const double s = sqrt(2.0 * var);
+    const double norm = sqrt(var) * 0.39894228040143267794;
+    double E[23], R[23];
+    for (int k = 0; k < 2 * W + 3; ++k) {
+        const double p = (double)(k - W - 1);
+        E[k] = exp(-(p * p) / (2.0 * var));
+        R[k] = erf(p / s);
+    }
+    for (int v = 0; v <= 2 * W; ++v) {
+        const double u = (double)(v - W), um = u - 1.0, up = u + 1.0;
+        const double e = E[v] - 2.0 * E[v + 1] + E[v + 2];
+        const double eu = R[v + 1];
+        out[v] = norm * e + 0.5 * um * (R[v] - eu) + 0.5 * up * (R[v + 2] - eu);
+    }
+}
+
 // Root of Eq. (lambda_eq) in the printed form: root 1 takes the '+' sign of
 // the square root, root 2 (the paper's choice) the '-' sign.
 __device__ inline double lambda_root(double mu2, double mu4, int root) {

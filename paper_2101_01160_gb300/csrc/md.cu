@@ -186,7 +186,9 @@ __global__ void k_nc_of_id(SysDev S, int32_t *nc_of_id) {
 
 
 // ---------------------------------------------------------------- batched f_eq stage
-// For every replica (one CTA each), on the device: the measured equilibrium
+// For every replica, on the device (k_feq_params: the moments and lambda;
+// k_feq_terms: the WSG sums over the Poisson window, split over CTAs;
+// k_feq_batch: one CTA per replica for the rest): the measured equilibrium
 // (Eq. theory_feq per particle, optionally averaged over symmetric sets),
 // the moments mu2, mu4 and a^2 (Eq. a2_n_ua), lambda from Eq. (lambda_eq)
 // (root 2), the Gaussian (Eq. feq_gaussian) and WSG (Eq. f_eq_wsg)
@@ -205,16 +207,26 @@ struct FeqBatchArgs {
     double *out;                   // [nrep][3 nb + FEQB_STATS]
 };
 
-__global__ void __launch_bounds__(FEQB_THREADS) k_feq_batch(FeqBatchArgs A) {
-    __shared__ double s_a[FEQB_THREADS], s_b[FEQB_THREADS], s_c[FEQB_THREADS], s_d[FEQB_THREADS];
-    __shared__ double s_par[4];
-    const int r = blockIdx.x, tid = threadIdx.x;
-    const RepDev &R = A.reps[r];
-    const int stride = 3 * A.nb + FEQB_STATS;
-    double *out = A.out + (long long)r * stride;
-    const int32_t *hist = A.hist + ((((long long)r * A.n_lg + A.lg) * A.n_dx + A.dxi) * MD_NBLK) * A.nb;
+// The WSG sum of one replica is spread over up to FEQB_SPLIT CTAs of
+// FEQB_SPLIT_TERMS Poisson terms each (the last takes any remainder): with
+// lambda capped at 1e5 the window holds at most 7,631 terms, and a single
+// CTA would carry them all on one SM's FP64 pipe.
+constexpr int FEQB_SPLIT = 64;
+constexpr int FEQB_SPLIT_TERMS = FEQB_THREADS;
+
+// Splits that hold terms for lambda (the others add nothing).
+__device__ inline int feqb_splits_used(double lam) {
+    const int n = wsg_cmax(lam) - wsg_cmin(lam) + 1;
+    return min(FEQB_SPLIT, (n + FEQB_SPLIT_TERMS - 1) / FEQB_SPLIT_TERMS);
+}
+
+// Moments, a^2 and lambda of replica r into s_par = {mu2, a^2, lambda}
+// (every thread calls it; s_a, s_b: FEQB_THREADS doubles of scratch); with
+// out != nullptr thread 0 also writes the replica's statistics.
+__device__ void feqb_params(const FeqBatchArgs &A, const RepDev &R, int r, double *s_a, double *s_b,
+                            double *s_par, double *out) {
+    const int tid = threadIdx.x;
     const double samples = (double)R.n * (double)A.nwin;
-    // moments
     double m2 = 0.0, m4 = 0.0;
     for (int g = R.pbase / 32 + tid; g < (R.pbase + R.cap) / 32; g += FEQB_THREADS) {
         m2 += A.mom[((long long)g * A.n_lg + A.lg) * 2];
@@ -251,41 +263,62 @@ __global__ void __launch_bounds__(FEQB_THREADS) k_feq_batch(FeqBatchArgs A) {
         s_par[0] = mu2;
         s_par[1] = mu2 / (dx * dx);
         s_par[2] = lam;
-        out[3 * A.nb + 0] = mu2;
-        out[3 * A.nb + 1] = mu4;
-        out[3 * A.nb + 2] = s_par[1];
-        out[3 * A.nb + 3] = lam;
-        out[3 * A.nb + 8] = (double)A.nwin;
-        out[3 * A.nb + 9] = samples;
-        out[3 * A.nb + 10] = (double)A.ovf[((long long)r * A.n_lg + A.lg) * A.n_dx + A.dxi];
-        out[3 * A.nb + 11] = dx;
-        out[3 * A.nb + 12] = st;
+        if (out) {
+            out[3 * A.nb + 0] = mu2;
+            out[3 * A.nb + 1] = mu4;
+            out[3 * A.nb + 2] = s_par[1];
+            out[3 * A.nb + 3] = lam;
+            out[3 * A.nb + 8] = (double)A.nwin;
+            out[3 * A.nb + 9] = samples;
+            out[3 * A.nb + 10] = (double)A.ovf[((long long)r * A.n_lg + A.lg) * A.n_dx + A.dxi];
+            out[3 * A.nb + 11] = dx;
+            out[3 * A.nb + 12] = st;
+        }
     }
     __syncthreads();
-    const double a2 = s_par[1], lam = s_par[2];
-    const int side = 2 * A.W + 1;
-    // WSG: Poisson terms in chunks of FEQB_THREADS; the 1D factors of one
-    // term are evaluated once for the 2W+1 displacements and shared by all
-    // classes (the 2D value is their outer product).  Each class sums the
-    // terms in increasing c.
+}
+
+constexpr int FEQB_CPT = ((2 * MD_MAX_W + 1) * (2 * MD_MAX_W + 1) + FEQB_THREADS - 1) / FEQB_THREADS;
+
+// One CTA per replica: par[4 r + {0, 1, 2}] = mu2, a^2, lambda.
+__global__ void __launch_bounds__(FEQB_THREADS) k_feq_params(FeqBatchArgs A, double *par) {
+    __shared__ double s_a[FEQB_THREADS], s_b[FEQB_THREADS], s_par[4];
+    const int r = blockIdx.x;
+    feqb_params(A, A.reps[r], r, s_a, s_b, s_par, nullptr);
+    if (threadIdx.x < 3) par[4 * r + threadIdx.x] = s_par[threadIdx.x];
+}
+
+// Grid (replica, split): the split's Poisson terms c, one per thread in
+// chunks of FEQB_THREADS; the 1D factors of one term are evaluated once for
+// the 2W+1 displacements and shared by all classes (the 2D value is their
+// outer product); each class sums the chunk's terms in increasing c.
+// part[(r * FEQB_SPLIT + split) * nb + i] = the split's partial sum, written
+// by the splits that hold terms (feqb_splits_used); the others return at
+// once.
+__global__ void __launch_bounds__(FEQB_THREADS) k_feq_terms(FeqBatchArgs A, const double *par,
+                                                            double *part) {
     __shared__ double s_w[FEQB_THREADS];
     __shared__ double s_F[FEQB_THREADS][2 * MD_MAX_W + 1];
-    constexpr int CPT = ((2 * MD_MAX_W + 1) * (2 * MD_MAX_W + 1) + FEQB_THREADS - 1) / FEQB_THREADS;
-    double accW[CPT];
+    const int r = blockIdx.x, split = blockIdx.y, tid = threadIdx.x;
+    const double a2 = par[4 * r + 1], lam = par[4 * r + 2];
+    if (split >= feqb_splits_used(lam)) return;
+    const int side = 2 * A.W + 1;
+    double accW[FEQB_CPT];
 #pragma unroll
-    for (int q = 0; q < CPT; ++q) accW[q] = 0.0;
+    for (int q = 0; q < FEQB_CPT; ++q) accW[q] = 0.0;
     const int cmin = wsg_cmin(lam), cmax = wsg_cmax(lam);
-    for (int c0 = cmin; c0 <= cmax && a2 > 0; c0 += FEQB_THREADS) {
+    const int lo = cmin + split * FEQB_SPLIT_TERMS;
+    const int hi = split == FEQB_SPLIT - 1 ? cmax : min(cmax, lo + FEQB_SPLIT_TERMS - 1);
+    for (int c0 = lo; c0 <= hi && a2 > 0; c0 += FEQB_THREADS) {
         const int c = c0 + tid;
-        if (c <= cmax) {
-            const double var = a2 * ((double)c + 1.0) / (lam + 1.0);
+        if (c <= hi) {
             s_w[tid] = poisson_weight(c, lam);
-            for (int v = 0; v < side; ++v) s_F[tid][v] = cell_gauss_1d((double)(v - A.W), var);
+            cell_gauss_row(a2 * ((double)c + 1.0) / (lam + 1.0), A.W, s_F[tid]);
         }
         __syncthreads();
-        const int nterm = min(FEQB_THREADS, cmax - c0 + 1);
+        const int nterm = min(FEQB_THREADS, hi - c0 + 1);
 #pragma unroll
-        for (int q = 0; q < CPT; ++q) {
+        for (int q = 0; q < FEQB_CPT; ++q) {
             const int i = tid + q * FEQB_THREADS;
             if (i < A.nb) {
                 const int ix = i % side, iy = i / side;
@@ -295,6 +328,43 @@ __global__ void __launch_bounds__(FEQB_THREADS) k_feq_batch(FeqBatchArgs A) {
             }
         }
         __syncthreads();
+    }
+    double *dst = part + ((long long)r * FEQB_SPLIT + split) * A.nb;
+#pragma unroll
+    for (int q = 0; q < FEQB_CPT; ++q) {
+        const int i = tid + q * FEQB_THREADS;
+        if (i < A.nb) dst[i] = accW[q];
+    }
+}
+
+// One CTA per replica: the statistics, the WSG sum of the splits' partials
+// (in split order), the measured and Gaussian equilibria and the distances.
+__global__ void __launch_bounds__(FEQB_THREADS) k_feq_batch(FeqBatchArgs A, const double *part) {
+    __shared__ double s_a[FEQB_THREADS], s_b[FEQB_THREADS], s_c[FEQB_THREADS], s_d[FEQB_THREADS];
+    __shared__ double s_par[4];
+    const int r = blockIdx.x, tid = threadIdx.x;
+    const RepDev &R = A.reps[r];
+    const int stride = 3 * A.nb + FEQB_STATS;
+    double *out = A.out + (long long)r * stride;
+    const int32_t *hist = A.hist + ((((long long)r * A.n_lg + A.lg) * A.n_dx + A.dxi) * MD_NBLK) * A.nb;
+    const double samples = (double)R.n * (double)A.nwin;
+    feqb_params(A, R, r, s_a, s_b, s_par, out);
+    const double a2 = s_par[1];
+    const int side = 2 * A.W + 1;
+    const int used = feqb_splits_used(s_par[2]);
+    // the Gaussian's 1D factors, one row shared by all classes
+    __shared__ double s_G[2 * MD_MAX_W + 1];
+    if (tid == 0 && a2 > 0) cell_gauss_row(a2, A.W, s_G);
+    __syncthreads();
+    constexpr int CPT = FEQB_CPT;
+    double accW[CPT];
+#pragma unroll
+    for (int q = 0; q < CPT; ++q) {
+        const int i = tid + q * FEQB_THREADS;
+        double acc = 0.0;
+        if (i < A.nb && a2 > 0)
+            for (int sp = 0; sp < used; ++sp) acc += part[((long long)r * FEQB_SPLIT + sp) * A.nb + i];
+        accW[q] = acc;
     }
     double mg = 0.0, kg = 0.0, mw = 0.0, kw = 0.0, sum = 0.0;
 #pragma unroll
@@ -316,8 +386,7 @@ __global__ void __launch_bounds__(FEQB_THREADS) k_feq_batch(FeqBatchArgs A) {
         for (int b = 0; b < MD_NBLK; ++b)
             for (int m = 0; m < nm; ++m) tot += hist[b * A.nb + mem[m]];
         const double P = samples > 0 ? (double)tot / ((double)nm * samples) : 0.0;
-        const double vx = (double)(i % side - A.W), vy = (double)(i / side - A.W);
-        const double G = a2 > 0 ? cell_gauss_1d(vx, a2) * cell_gauss_1d(vy, a2) : 0.0;
+        const double G = a2 > 0 ? s_G[i % side] * s_G[i / side] : 0.0;
         const double Wg = accW[q];
         out[i] = P;
         out[A.nb + i] = G;
@@ -387,6 +456,8 @@ struct md_system {
     Control *d_ctl = nullptr;
     double *d_epart = nullptr;
     double *d_small = nullptr;   // readout scratch (2*nb + 8 doubles, 4 energy)
+    double *d_feq_part = nullptr;   // WSG partial sums of the f_eq stage [nrep][FEQB_SPLIT][nb]
+    double *d_feq_par = nullptr;    // per replica mu2, a^2, lambda of the f_eq stage [nrep][4]
     long long *d_hist64 = nullptr;
     int32_t *d_nc_of_id = nullptr;
 };
@@ -736,6 +807,8 @@ int md_init_batch(const md_params *p, int32_t n_rep, const double *x, const doub
     ALLOC(S.mom, sizeof(double) * ngr * nlg * 2);
     ALLOC(s->d_epart, sizeof(double) * ngr * 4);
     ALLOC(s->d_small, sizeof(double) * (2 * s->nb + 16));
+    ALLOC(s->d_feq_part, sizeof(double) * (size_t)n_rep * FEQB_SPLIT * s->nb);
+    ALLOC(s->d_feq_par, sizeof(double) * 4 * (size_t)n_rep);
     ALLOC(s->d_hist64, sizeof(long long) * s->nb);
     ALLOC(s->d_nc_of_id, sizeof(int32_t) * s->ntot);
 #undef ALLOC
@@ -1025,7 +1098,9 @@ int feq_batch(md_system *s, int32_t lg, int32_t dxi, int32_t symmetrize, double 
     double *dst = out;
     if (!dev) MD_CUDA_TRY(cudaMallocAsync((void **)&dst, bytes, s->st));
     A.out = dst;
-    k_feq_batch<<<s->nrep, FEQB_THREADS, 0, s->st>>>(A);
+    k_feq_params<<<s->nrep, FEQB_THREADS, 0, s->st>>>(A, s->d_feq_par);
+    k_feq_terms<<<dim3(s->nrep, FEQB_SPLIT), FEQB_THREADS, 0, s->st>>>(A, s->d_feq_par, s->d_feq_part);
+    k_feq_batch<<<s->nrep, FEQB_THREADS, 0, s->st>>>(A, s->d_feq_part);
     cudaError_t e = cudaGetLastError();
     if (!dev) {
         if (e == cudaSuccess) e = cudaMemcpyAsync(out, dst, bytes, cudaMemcpyDeviceToHost, s->st);
