@@ -150,6 +150,19 @@ def ensemble(seed_offset=0, reps=None):
     return out
 
 
+WORKLOAD = (f"batched ensemble: {N_REP} replicas, N log-uniform [4096,65536], phi U[0.02,0.30], "
+            f"T U[1,20], FP32 cell+offset, dt 5e-4, Verlet skin {SKIN}, sampling every 400 steps "
+            "(dt_lg 0.2) on dx~1, W=4; 400 MD steps + batched f_eq stage per step")
+
+
+def _ensemble_particles(seed_offset=0):
+    """Total particle count of the ensemble (no states built)."""
+    from paper_2101_01160_gb300 import inputs
+
+    Ns, _, _ = inputs.ensemble_params(N_REP, seed=ENS_SEED + seed_offset)
+    return int(sum(int(n) for n in Ns))
+
+
 def _ens_params(mdlg, ens, prec):
     return [mdlg.make_params(n, L, dt=DT, precision=prec, W=W, n_equil=0, lg_every=(EVERY,),
                              lx=(int(round(L)),), skin=SKIN) for (n, L, _, _, _) in ens]
@@ -426,10 +439,7 @@ def run_ours(args):
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": f"batched ensemble: {N_REP} replicas, N log-uniform "
-                               "[4096,65536], phi U[0.02,0.30], T U[1,20], FP32 cell+offset, "
-                               f"dt 5e-4, Verlet skin {SKIN}, sampling every 400 steps (dt_lg 0.2) on dx~1, W=4; "
-                               "400 MD steps + batched f_eq stage per step",
+        "config": {"workload": WORKLOAD,
                    "n_particles": ntot, "md_steps_per_step": MD_PER_STEP,
                    "l2": "flushed between timed steps (256 MB write)",
                    "launch_shape": {"block_threads": shape[0], "per_thread": shape[1],
@@ -502,7 +512,8 @@ def run_reference(args):
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
-        "config": {"workload": "batched ensemble (oracle sample)", "md_steps_per_step": 100},
+        "config": {"workload": WORKLOAD, "n_particles": _ensemble_particles(),
+                   "md_steps_per_step": MD_PER_STEP, "parallelism": "one host core"},
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
                          "sample": sample},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
