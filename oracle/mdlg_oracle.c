@@ -221,9 +221,10 @@ void or_collision(const int64_t *nt, const int64_t *nn, int64_t lx, int32_t W, i
  *     delta = wrap(c1 - c0) * h + (off1 - off0),
  * which has a single rounding (none in the product and the offset
  * difference when the offsets are FP32), instead of decoding two absolute
- * positions near the box size.  Its bin is floor(delta * (1 / width)) +
- * nbins / 2, with 1 / width rounded once; bin k covers roughly
- * [(k - nbins/2) width, (k - nbins/2 + 1) width).  Values outside all bins
+ * positions near the box size.  Its bin is floor(delta / width) + nbins / 2:
+ * bin k covers [(k - nbins/2) width, (k - nbins/2 + 1) width), the bins
+ * X_i whose model masses or_pdf_gauss_bins and or_pdf_wsg_bins integrate,
+ * and a value on an edge belongs to the upper bin.  Values outside all bins
  * count in *outside, so sum(hist) + *outside = 2n.  Accumulates. */
 int or_disp_hist(int64_t n, const int32_t *c0, const void *ox0, const void *oy0,
                  const int32_t *c1, const void *ox1, const void *oy1, int32_t f64,
@@ -231,7 +232,6 @@ int or_disp_hist(int64_t n, const int32_t *c0, const void *ox0, const void *oy0,
                  int64_t *hist, int64_t *outside)
 {
     (void)L;
-    double inv_w = 1.0 / width;
     for (int64_t j = 0; j < n; ++j) {
         int32_t cell0[2] = {c0[j] % ncell, c0[j] / ncell};
         int32_t cell1[2] = {c1[j] % ncell, c1[j] / ncell};
@@ -243,7 +243,7 @@ int or_disp_hist(int64_t n, const int32_t *c0, const void *ox0, const void *oy0,
             double a = f64 ? ((const double *)o0[axis])[j] : (double)((const float *)o0[axis])[j];
             double b = f64 ? ((const double *)o1[axis])[j] : (double)((const float *)o1[axis])[j];
             double d = (double)dc * h + (b - a);
-            double k = floor(d * inv_w) + (double)(nbins / 2);
+            double k = floor(d / width) + (double)(nbins / 2);
             if (k >= 0.0 && k < (double)nbins)
                 hist[(int64_t)k] += 1;
             else

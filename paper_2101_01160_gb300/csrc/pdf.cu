@@ -6,13 +6,12 @@
 //
 // The displacement is taken in the cell frame, wrap(c1 - c0) * h +
 // (off1 - off0) with the cell difference wrapped to the nearest image, and
-// its bin is floor(delta * (1 / width)), every operation of that FP64
-// definition rounded on its own.  The kernel decides the bin in FP32 with a
-// proven error bound and falls back to the FP64 definition only near bin
-// edges (GB300's FP64 rate is a small fraction of its FP32 rate), so bin
-// indices are exact.  The histogram is privatised per CTA in shared memory
-// and flushed with 64-bit atomics: integer counts do not depend on the
-// launch.
+// its bin is floor(delta / width), every operation of that FP64 definition
+// rounded on its own.  The kernel decides the bin in FP32 with a proven
+// error bound and falls back to the FP64 definition only near bin edges
+// (GB300's FP64 rate is a small fraction of its FP32 rate), so bin indices
+// are exact.  The histogram is privatised per CTA in shared memory and
+// flushed with 64-bit atomics: integer counts do not depend on the launch.
 #include <cmath>
 
 #include "common.cuh"
@@ -29,30 +28,31 @@ struct PdfSnap {
     int f64;
 };
 
-// Bin index of one displacement component, floor(RN(d * inv_w)) with d =
+// Bin index of one displacement component, floor(RN(d / w)) with d =
 // RN(RN(dc * h) + RN(o1 - o0)) in FP64 (the definition), decided in FP32
 // wherever FP32 provably gives the same integer.  With a = RN32(dc * hf),
-// hf = RN32(h), invwf = RN32(inv_w):
+// hf = RN32(h), invwf = RN32(1 / w):
 //     q = RN32(RN32(a + RN32(o1 - o0)) * invwf),
 //     S = RN32((|a| + |o1| + |o0|) * invwf),
-// q differs from (dc h + o1 - o0) inv_w by less than 0.875 S 2^-21 (two
-// roundings of dc h, one of the offset difference, one of the sum, two of
-// the product, one per offset if they are FP64 -- each at most 2^-24
-// relative to |a| + |o1| + |o0|), and the FP64 value by a few 2^-53 of the
-// same.  So when q is more than S 2^-20 from the nearest integer, floor(q)
-// is the bin; otherwise (values on or within about S 1e-6 of a bin edge) the
-// FP64 evaluation decides.  Bit-identical to the FP64 definition for finite
-// inputs.
+// q differs from the exact quotient (dc h + o1 - o0) / w by less than
+// S 2^-21 (two roundings of dc h, one of the offset difference, one of the
+// sum, two of the product with the rounded reciprocal, one per offset if
+// they are FP64 -- each at most 2^-24 relative to |a| + |o1| + |o0|), and
+// the FP64 definition lies within a few 2^-53 of the same magnitude of that
+// quotient.  So when q is more than S 2^-20 from the nearest integer, no
+// integer separates the two and floor(q) is the bin; otherwise (values on or
+// within about S 1e-6 of a bin edge) the FP64 division decides.
+// Bit-identical to the FP64 definition for finite inputs.
 // The FP64 definition, out of line (it runs only near bin edges).
-__device__ __noinline__ long long disp_bin_slow(int dc, double o1, double o0, double h, double inv_w) {
+__device__ __noinline__ long long disp_bin_slow(int dc, double o1, double o0, double h, double w) {
     const double doff = __dsub_rn(o1, o0);
     const double d = __dadd_rn(__dmul_rn((double)dc, h), doff);
     // floor as an integer in one round-down conversion
-    return __double2ll_rd(__dmul_rn(d, inv_w));
+    return __double2ll_rd(__ddiv_rn(d, w));
 }
 
 template <typename T>
-__device__ __forceinline__ long long disp_bin(int dc, T o1, T o0, double h, float hf, double inv_w,
+__device__ __forceinline__ long long disp_bin(int dc, T o1, T o0, double h, float hf, double w,
                                               float invwf) {
     const float a = __fmul_rn((float)dc, hf);
     const float f1 = (float)o1, f0 = (float)o0;
@@ -62,7 +62,7 @@ __device__ __forceinline__ long long disp_bin(int dc, T o1, T o0, double h, floa
     // run on the FP64 pipe)
     if (S < 0x1p22f && fabsf(__fsub_rn(q, rintf(q))) > __fmul_rn(S, 0x1p-20f))
         return __float2int_rd(q);
-    return disp_bin_slow(dc, (double)o1, (double)o0, h, inv_w);
+    return disp_bin_slow(dc, (double)o1, (double)o0, h, w);
 }
 
 template <typename T> struct PdfVec4;
@@ -83,7 +83,7 @@ template <> struct PdfVec4<double> {
 struct DispParams {
     int ncell, nbins;
     float inv_ncell, hf, invwf;
-    double h, inv_w;
+    double h, w;
 };
 
 // Counts both displacement components of one particle into the CTA's bins.
@@ -100,7 +100,7 @@ __device__ __forceinline__ void disp_count(const DispParams &P, int c0, int c1, 
         int dc = cc1[ax] - cc0[ax];
         if (dc > P.ncell / 2) dc -= P.ncell;
         if (dc < -(P.ncell / 2)) dc += P.ncell;
-        const long long k = disp_bin<T>(dc, o1[ax], o0[ax], P.h, P.hf, P.inv_w, P.invwf);
+        const long long k = disp_bin<T>(dc, o1[ax], o0[ax], P.h, P.hf, P.w, P.invwf);
         if (k >= lo && k < hi)
             atomicAdd(&sh_bins[(int)(k - lo)], 1u);
         else
@@ -211,9 +211,9 @@ extern "C" int mdlg_disp_hist(const md_snapshot *t0, const md_snapshot *t1, int6
     P.ncell = t0->ncell;
     P.nbins = nbins;
     P.h = t0->h;
-    P.inv_w = 1.0 / width;
+    P.w = width;
     P.hf = (float)t0->h;
-    P.invwf = (float)P.inv_w;
+    P.invwf = (float)(1.0 / width);
     P.inv_ncell = 1.0f / (float)t0->ncell;
     const size_t smem = sizeof(unsigned) * nbins;
     auto al16 = [](const void *p) { return ((uintptr_t)p & 15u) == 0; };

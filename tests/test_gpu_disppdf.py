@@ -61,6 +61,49 @@ def test_disp_hist_edges_and_wrap(mdlg, orc):
     assert np.array_equal(hist.cpu().numpy(), rh) and int(out.item()) == ro == 1
 
 
+@pytest.mark.parametrize("f64", [False, True])
+def test_disp_hist_bin_edges_ulps(mdlg, orc, f64):
+    """Displacements placed on bin edges k * width and 1-3 ulp of the stored
+    offset to either side: the GPU bin of floor(delta / width) equals the
+    oracle's on every one (the FP32 decision's guard sends these to the FP64
+    division)."""
+    ft = np.float64 if f64 else np.float32
+    ncell, nbins = 64, 512
+    h = float(ft(3.1))
+    rng = np.random.default_rng(21 + f64)
+    n = 7 * 4096
+    for width in (0.05, 0.25, 1.0 / 3.0):
+        c0 = rng.integers(0, ncell * ncell, n)
+        o0x = rng.uniform(0.0, h, n).astype(ft)
+        o0y = rng.uniform(0.0, h, n).astype(ft)
+        k = rng.integers(-nbins // 2 + 1, nbins // 2 - 1, (2, n))
+        dc = rng.integers(-2, 3, (2, n))
+        m = np.repeat(np.arange(-3, 4), n // 7)            # ulps from the edge
+        o1 = []
+        for ax, o0 in enumerate((o0x, o0y)):
+            target = k[ax] * width - dc[ax] * h + o0.astype(np.float64)
+            v = target.astype(ft)
+            for step in range(3):                         # walk m ulps away
+                up = m > step
+                dn = m < -step
+                v = np.where(up, np.nextafter(v, ft(np.inf)), v)
+                v = np.where(dn, np.nextafter(v, ft(-np.inf)), v)
+            o1.append(v.astype(ft))
+        cx0, cy0 = c0 % ncell, c0 // ncell
+        cx1 = (cx0 + dc[0]) % ncell
+        cy1 = (cy0 + dc[1]) % ncell
+        sn = dict(cell0=c0.astype(np.int32), ox0=o0x, oy0=o0y,
+                  cell1=(cy1 * ncell + cx1).astype(np.int32), ox1=o1[0], oy1=o1[1])
+        hist, outc = mdlg.disp_hist(*[_dev(sn[kk]) for kk in KEYS], ncell, h, width, nbins)
+        rh, ro = orc.disp_hist(sn, ncell, h, ncell * h, width, nbins)
+        assert np.array_equal(hist.cpu().numpy(), rh), width
+        assert int(outc.item()) == ro
+        # the edges really are hit: the displacements straddle them
+        d = dc[0] * h + (o1[0].astype(np.float64) - o0x.astype(np.float64))
+        assert np.mean(np.floor(d / width) == k[0]) > 0.3
+        assert np.mean(np.floor(d / width) == k[0] - 1) > 0.3
+
+
 def test_disp_hist_rejects_bad_args(mdlg):
     c = torch.zeros(4, dtype=torch.int32, device="cuda")
     o = torch.zeros(4, dtype=torch.float32, device="cuda")
