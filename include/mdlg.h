@@ -201,6 +201,17 @@ int md_autotune(md_system *s, int64_t steps_per_trial, int32_t *best3);
  * clears it). */
 int md_sync(md_system *s);
 
+/* Failure-detection self-test of the bounded grid barrier (no counterpart in
+ * the paper).  Runs one MD step launch in which CTA 0 leaves the kernel
+ * instead of arriving at the step's grid barrier, with the barrier wait
+ * limited to limit_s seconds (0 < limit_s <= 4): the other CTAs give up
+ * after limit_s, flag the timeout and leave, and the call returns
+ * MD_E_TIMEOUT (MD_OK would mean the limit failed).  Nothing faults or
+ * hangs; the barrier's arrival count is cleared afterwards, but the
+ * particle state is that of an aborted step: destroy the system.  Needs a
+ * launch of at least 2 CTAs.  Synchronises. */
+int md_barrier_selftest(md_system *s, double limit_s);
+
 int md_info(md_system *s, md_info_t *out);
 int md_rep_info(md_system *s, int32_t rep, md_rep_info_t *out);
 
@@ -228,6 +239,17 @@ int md_get_snapshot(md_system *s, int32_t lg, int32_t *cell, void *off_x, void *
  * outputs; fabs_sum (may be NULL) receives sum_j |F_ij| per particle.
  * Synchronises. */
 int md_forces(md_system *s, double *fx, double *fy, double *fabs_sum);
+
+/* Advances nsteps >= 1 steps exactly as md_step(s, nsteps) does (the same
+ * kernel and launch shape, the same trajectory bit for bit) and returns, by
+ * particle id, the Lennard-Jones force (Sec. 4) that the last step's force
+ * pass summed over the Verlet neighbour lists at the positions of step
+ * nsteps - 1 (those that md_get_raw returned just before the call when
+ * nsteps = 1).  This is the arithmetic of every ordinary step, including
+ * lists built several steps earlier; md_forces instead evaluates the force
+ * from the current cell list.  fx, fy: host or device, FP64, [n_total].
+ * Synchronises. */
+int md_step_forces(md_system *s, int64_t nsteps, double *fx, double *fy);
 
 /* Energy of replica rep at the current step: out4 = {kinetic, shifted
  * potential, P_x, P_y} (host, FP64).  Synchronises. */

@@ -581,6 +581,9 @@ int sync_status(md_system *s) {
     MD_CUDA_TRY(cudaMemcpy(&ds, &s->d_ctl->status, sizeof(int), cudaMemcpyDeviceToHost));
     if (ds) {
         MD_CUDA_TRY(cudaMemset(&s->d_ctl->status, 0, sizeof(int)));
+        // a wait that gave up leaves the arrival count behind; no kernel of
+        // the system runs now, so it is cleared for the next launch
+        if (ds & DS_TIMEOUT) MD_CUDA_TRY(cudaMemset(&s->d_ctl->bar_count, 0, sizeof(unsigned)));
         return status_to_code(ds);
     }
     return MD_OK;
@@ -836,6 +839,7 @@ int md_init_batch(const md_params *p, int32_t n_rep, const double *x, const doub
     S.ntot = s->ntot;
     S.K = s->K;
     S.timeout_ns = 4000000000ull;
+    S.dbg_leave_cta = -1;
     auto tryc = [&](cudaError_t er) {
         if (er != cudaSuccess && rc == MD_OK) rc = fail(MD_E_CUDA, "md_init_batch: %s", cudaGetErrorString(er));
     };
@@ -891,6 +895,21 @@ int md_tune(md_system *s, int32_t block_threads, int32_t per_thread, int32_t sta
     if (per_thread == 0) per_thread = default_ppt(s);
     if (staging == 0) staging = 1;
     return configure_launch(s, block_threads, per_thread, staging);
+}
+
+int md_barrier_selftest(md_system *s, double limit_s) {
+    if (!s || !(limit_s > 0.0) || !(limit_s <= 4.0)) return fail(MD_E_ARG, "md_barrier_selftest: bad arguments");
+    if (s->grid < 2) return fail(MD_E_ARG, "md_barrier_selftest: needs a launch of at least 2 CTAs");
+    int rc = sync_status(s);
+    if (rc) return rc;
+    const uint64_t keep = s->sd.timeout_ns;
+    s->sd.timeout_ns = (uint64_t)(limit_s * 1e9);
+    s->sd.dbg_leave_cta = 0;
+    rc = md_step(s, 1);
+    s->sd.dbg_leave_cta = -1;
+    s->sd.timeout_ns = keep;
+    if (rc) return rc;
+    return sync_status(s);
 }
 
 int md_sync(md_system *s) {
@@ -989,6 +1008,25 @@ int md_forces(md_system *s, double *fx, double *fy, double *fabs_sum) {
         if (!dst[k]) continue;
         cudaError_t e = cudaMemcpyAsync(dst[k], tmp + k * s->ntot, bytes, cudaMemcpyDefault, s->st);
         if (e != cudaSuccess) rc = fail(MD_E_CUDA, "md_forces: %s", cudaGetErrorString(e));
+    }
+    cudaFreeAsync(tmp, s->st);
+    if (rc) return rc;
+    return sync_status(s);
+}
+
+int md_step_forces(md_system *s, int64_t nsteps, double *fx, double *fy) {
+    if (!s || nsteps < 1 || !fx || !fy) return fail(MD_E_ARG, "md_step_forces: bad arguments");
+    const size_t bytes = sizeof(double) * s->ntot;
+    double *tmp = nullptr;
+    MD_CUDA_TRY(cudaMallocAsync((void **)&tmp, 2 * bytes, s->st));
+    s->sd.dbg_fx = tmp;
+    s->sd.dbg_fy = tmp + s->ntot;
+    int rc = md_step(s, nsteps);
+    s->sd.dbg_fx = s->sd.dbg_fy = nullptr;
+    double *dst[2] = {fx, fy};
+    for (int k = 0; k < 2 && rc == MD_OK; ++k) {
+        cudaError_t e = cudaMemcpyAsync(dst[k], tmp + k * s->ntot, bytes, cudaMemcpyDefault, s->st);
+        if (e != cudaSuccess) rc = fail(MD_E_CUDA, "md_step_forces: %s", cudaGetErrorString(e));
     }
     cudaFreeAsync(tmp, s->st);
     if (rc) return rc;

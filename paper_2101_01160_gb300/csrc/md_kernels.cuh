@@ -92,6 +92,12 @@ struct SysDev {
     double *mom;                // [nslots/32][n_lg][2]
     long long ntot;
     uint64_t timeout_ns;
+    // force of the last step's force pass by particle id (md_step_forces), or
+    // NULL in ordinary steps
+    double *dbg_fx, *dbg_fy;
+    // md_barrier_selftest: this CTA leaves the kernel instead of arriving at
+    // the first step's grid barrier (-1 in every other launch)
+    int32_t dbg_leave_cta;
 };
 
 // largest staged position window of a chunk (12 KB FP32, 24 KB FP64)
@@ -697,6 +703,14 @@ __host__ __device__ inline size_t smem_bytes(int n_lg, int n_dx, int nb, int chu
            (staged ? 2 * stage_bytes<T>(chunk) : 0);
 }
 
+// Records the force of one slot by particle id (md_step_forces only).
+template <typename T>
+__device__ __forceinline__ void debug_force(const SysDev &S, int set, int slot, T fx, T fy) {
+    const int id = S.pid[set][slot];
+    S.dbg_fx[id] = (double)fx;
+    S.dbg_fy[id] = (double)fy;
+}
+
 // Velocity-Verlet update of one particle: v += (dt/2m) F twice (the first
 // kick completes the previous step unless velocities are at an integer
 // step), off += dt v into the other position buffer; tracks the largest
@@ -827,6 +841,7 @@ __global__ void __launch_bounds__(BLOCK, md_min_ctas(BLOCK, DENSE)) k_md_persist
                     T fx = T(0), fy = T(0);
                     lj_list<T>(S, R, d, B.pos, B.ent + (li >> 5) * NB_STAGE<T> * 32 + (li & 31), pin,
                                oi, slot, B.nn[li], fx, fy);
+                    if (S.dbg_fx && it == nsteps - 1) debug_force(S, set, slot, fx, fy);
                     kick_drift<T>(R, oi, B.vel[li], fx, fy, hk, dt, first, vscale, pout, vel, slot, vm,
                                   bad);
                 }
@@ -846,6 +861,7 @@ __global__ void __launch_bounds__(BLOCK, md_min_ctas(BLOCK, DENSE)) k_md_persist
                     const V vi = vel[slot];   // requested now, used after the force sum
                     T fx = T(0), fy = T(0);
                     lj_list<T>(S, R, none, nullptr, nullptr, pin, oi, slot, S.nn[slot], fx, fy);
+                    if (S.dbg_fx && it == nsteps - 1) debug_force(S, set, slot, fx, fy);
                     kick_drift<T>(R, oi, vi, fx, fy, hk, dt, first, vscale, pout, vel, slot, vm, bad);
                 }
             }
@@ -858,6 +874,9 @@ __global__ void __launch_bounds__(BLOCK, md_min_ctas(BLOCK, DENSE)) k_md_persist
             for (int w = 0; w < BLOCK / 32; ++w) m = fmaxf(m, s_vmax[w]);
             atomicMax(&C->vmax[s % 3], __float_as_uint(m));   // non-negative floats order as uints
         }
+        // the barrier self-test: one CTA never arrives, so the others' wait
+        // runs into its limit (nothing else is skipped; the CTA returns)
+        if (it == 0 && S.dbg_leave_cta == (int)blockIdx.x) return;
         if (!grid_sync(bar, gen, S.timeout_ns)) return;
         cur ^= 1;
         // every CTA accumulates the same bound, in units of half the skin

@@ -72,6 +72,7 @@ _SIGS = {
     "md_destroy": ([P], None),
     "md_step": ([P, C.c_int64], C.c_int),
     "md_sync": ([P], C.c_int),
+    "md_barrier_selftest": ([P, C.c_double], C.c_int),
     "md_tune": ([P, C.c_int32, C.c_int32, C.c_int32], C.c_int),
     "md_autotune": ([P, C.c_int64, P], C.c_int),
     "md_info": ([P, C.POINTER(md_info_t)], C.c_int),
@@ -81,6 +82,7 @@ _SIGS = {
     "md_get_raw": ([P, P, P, P], C.c_int),
     "md_get_snapshot": ([P, C.c_int32, P, P, P], C.c_int),
     "md_forces": ([P, P, P, P], C.c_int),
+    "md_step_forces": ([P, C.c_int64, P, P], C.c_int),
     "md_energy": ([P, C.c_int32, P], C.c_int),
     "md_hist_raw": ([P, C.c_int32, C.c_int32, C.c_int32, P, P, P], C.c_int),
     "feq_measured": ([P, C.c_int32, C.c_int32, C.c_int32, C.c_int32, P, P,
@@ -209,6 +211,11 @@ class System:
     def sync(self):
         _check(load().md_sync(self.h))
 
+    def barrier_selftest(self, limit_s=0.02):
+        """Return code of md_barrier_selftest (MD_E_TIMEOUT when the bounded
+        barrier wait works); the system must be closed afterwards."""
+        return int(load().md_barrier_selftest(self.h, float(limit_s)))
+
     def tune(self, block_threads=0, per_thread=0, staging=0):
         _check(load().md_tune(self.h, block_threads, per_thread, staging))
 
@@ -259,6 +266,13 @@ class System:
         fx, fy, fa = (np.zeros(self.n_total) for _ in range(3))
         _check(load().md_forces(self.h, _ptr(fx), _ptr(fy), _ptr(fa)))
         return fx, fy, fa
+
+    def step_forces(self, nsteps=1):
+        """Advances nsteps and returns the list forces of the last step's
+        force pass, FP64 by particle id (md_step_forces)."""
+        fx, fy = np.zeros(self.n_total), np.zeros(self.n_total)
+        _check(load().md_step_forces(self.h, int(nsteps), _ptr(fx), _ptr(fy)))
+        return fx, fy
 
     def energy(self, rep=0):
         out = np.zeros(4)

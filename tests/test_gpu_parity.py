@@ -16,6 +16,7 @@ import numpy as np
 import pytest
 
 from paper_2101_01160_gb300 import inputs
+import _bars
 
 pytestmark = pytest.mark.gpu
 
@@ -164,17 +165,22 @@ def test_fused_binning_bitexact_on_snapshots(mdlg, orc, prec):
     s.step(2 * every)
     snaps = {k: [t.cpu().numpy() for t in s.get_snapshot(k)] for k in (0, 1)}
     before = {(k, d): s.hist_raw(0, k, d) for k in (0, 1) for d in (0, 1)}
+    m0 = _bars.moment_sums(s, 0, 1, n)
     s.step(2 * every)
     after_a = [t.cpu().numpy() for t in s.get_snapshot(0)]
+    b = snaps[1]
+    a = [t.cpu().numpy() for t in s.get_snapshot(1)]
+    sn = dict(cell0=b[0], ox0=b[1], oy0=b[2], cell1=a[0], ox1=a[1], oy1=a[2])
     for d, lx in enumerate(p.lx[:2]):
         h1, o1, _ = s.hist_raw(0, 1, d)
         h0, o0, _ = before[(1, d)]
-        b = snaps[1]
-        a = [t.cpu().numpy() for t in s.get_snapshot(1)]
-        sn = dict(cell0=b[0], ox0=b[1], oy0=b[2], cell1=a[0], ox1=a[1], oy1=a[2])
         rh, ro, _ = orc.bin_celloff(sn, nc, h, info.L_eff, lx, 4)
         assert np.array_equal(h1 - h0, rh)
         assert o1 - o0 == ro
+    # the fused moment sums of the window (Sec. 3(b)) against the oracle's
+    m1 = _bars.moment_sums(s, 0, 1, n)
+    (S2, S4), (b2, b4) = _bars.moment_bar(b, a, nc, h, info.L_eff, m0, m1)
+    assert abs((m1 - m0)[0] - S2) <= b2 and abs((m1 - m0)[1] - S4) <= b4
     assert after_a[0].shape == (n,)
     s.close()
 
@@ -415,7 +421,7 @@ def test_autotune_keeps_trajectory(mdlg):
     p = mdlg.make_params(n, L, precision=mdlg.MD_FP32_CELLOFF, lg_every=(50,), lx=(int(L),))
     a = mdlg.System(p, st.x, st.y, st.vx, st.vy)
     best = a.autotune(20)
-    assert best[0] in (128, 256) and best[1] in (1, 2, 4) and best[2] in (1, 2)
+    assert best[0] in (128, 256) and best[1] in (1, 2, 4) and best[2] in (1, 2, 3)
     done = a.info().step
     assert done > 0
     b = mdlg.System(p, st.x, st.y, st.vx, st.vy)
