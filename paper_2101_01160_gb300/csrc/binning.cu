@@ -9,6 +9,8 @@
 // and one atomic per distinct class is issued); the FP64 moment sums are
 // reduced per CTA into a scratch array and summed in CTA order by a second
 // one-block kernel, so the result does not depend on scheduling.
+#include <mutex>
+
 #include "common.cuh"
 #include "lattice.cuh"
 
@@ -145,19 +147,74 @@ int bin_launch(const md_snapshot *t0, const md_snapshot *t1, int64_t n, int32_t 
 constexpr int BIN_SCRATCH_CTAS = 2048;
 static __device__ __align__(256) double g_bin_scratch[2 * BIN_SCRATCH_CTAS];
 
+// CTAs of one binning launch: one per 256 particles, at most 8 per SM of
+// the current device (SM count queried per call: a process may bin on GPUs
+// of different sizes).
 int bin_grid(int64_t n) {
-    static int nsm = 0;
-    if (nsm == 0) {
-        int dev = 0;
-        cudaGetDevice(&dev);
-        cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-        if (nsm <= 0) nsm = 1;
-    }
+    int dev = 0, nsm = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || nsm <= 0)
+        nsm = 1;
     int64_t want = (n + 255) / 256;
     int64_t cap = (int64_t)nsm * 8;
     if (want > cap) want = cap;
     if (want < 1) want = 1;
     return (int)want;
+}
+
+// Device address of g_bin_scratch on the current device.  Looked up with
+// that device current on the first call made on it, and looked up again
+// when the device's context has changed since (after a cudaDeviceReset the
+// module is loaded afresh and the array may live elsewhere).  The table is
+// guarded by a mutex, so host threads may call concurrently.
+using CtxGetCurrentFn = int (*)(void **);
+constexpr int BIN_MAX_DEV = 64;
+struct ScratchSlot {
+    const void *ctx = nullptr;
+    double *ptr = nullptr;
+};
+std::mutex g_scratch_mu;
+ScratchSlot g_scratch[BIN_MAX_DEV];
+
+CtxGetCurrentFn ctx_get_current() {
+    static CtxGetCurrentFn fn = [] {
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q{};
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &p, 12000, cudaEnableDefault, &q) !=
+                cudaSuccess ||
+            q != cudaDriverEntryPointSuccess)
+            p = nullptr;
+        return reinterpret_cast<CtxGetCurrentFn>(p);
+    }();
+    return fn;
+}
+
+int scratch_address(double **out) {
+    int dev = 0;
+    MD_CUDA_TRY(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= BIN_MAX_DEV)
+        return fail(MD_E_LIMIT, "mdlg_bin_noalloc: device %d >= %d", dev, BIN_MAX_DEV);
+    const CtxGetCurrentFn get = ctx_get_current();
+    auto current = [get]() {
+        void *c = nullptr;
+        if (!get || get(&c) != 0) c = nullptr;
+        return c;
+    };
+    // no current context yet on this thread (or no way to ask): look up,
+    // which also makes the device's primary context current
+    const void *ctx = current();
+    std::lock_guard<std::mutex> lk(g_scratch_mu);
+    ScratchSlot &sl = g_scratch[dev];
+    if (!sl.ptr || !ctx || sl.ctx != ctx) {
+        double *p = nullptr;
+        const cudaError_t e = cudaGetSymbolAddress((void **)&p, g_bin_scratch);
+        if (e != cudaSuccess)
+            return fail(MD_E_CUDA, "mdlg_bin_noalloc: cudaGetSymbolAddress: %s", cudaGetErrorString(e));
+        sl.ptr = p;
+        sl.ctx = current();
+    }
+    *out = sl.ptr;
+    return MD_OK;
 }
 
 }  // namespace mdlg
@@ -185,9 +242,9 @@ extern "C" int mdlg_bin(const md_snapshot *t0, const md_snapshot *t1, int64_t n,
 
 // Same computation as mdlg_bin with the partials in g_bin_scratch.  The
 // array's device address is looked up on the first call on each device
-// (with that device current), so that first call should come before any
-// stream capture; nothing is allocated.  Calls that overlap on the GPU share
-// the array and race.
+// (with that device current), and again after a cudaDeviceReset, so that
+// first call should come before any stream capture; nothing is allocated.
+// Calls that overlap on the GPU share the array and race.
 extern "C" int mdlg_bin_noalloc(const md_snapshot *t0, const md_snapshot *t1, int64_t n, int32_t lx,
                                 int32_t W, int32_t *hist_out, int64_t *overflow_out, double *mom_out,
                                 void *stream) {
@@ -197,21 +254,12 @@ extern "C" int mdlg_bin_noalloc(const md_snapshot *t0, const md_snapshot *t1, in
     if (grid > BIN_SCRATCH_CTAS)
         return fail(MD_E_LIMIT, "mdlg_bin_noalloc: %d CTAs exceed the scratch capacity of %d", grid,
                     BIN_SCRATCH_CTAS);
-    constexpr int MAX_DEV = 64;
-    static double *scratch[MAX_DEV] = {};
-    int dev = 0;
-    MD_CUDA_TRY(cudaGetDevice(&dev));
-    if (dev < 0 || dev >= MAX_DEV) return fail(MD_E_LIMIT, "mdlg_bin_noalloc: device %d >= %d", dev, MAX_DEV);
-    if (!scratch[dev]) {
-        double *p = nullptr;
-        const cudaError_t e = cudaGetSymbolAddress((void **)&p, g_bin_scratch);
-        if (e != cudaSuccess)
-            return fail(MD_E_CUDA, "mdlg_bin_noalloc: cudaGetSymbolAddress: %s", cudaGetErrorString(e));
-        scratch[dev] = p;
-    }
+    double *scratch = nullptr;
+    rc = scratch_address(&scratch);
+    if (rc) return rc;
     cudaStream_t st = (cudaStream_t)stream;
     const int nb = (2 * W + 1) * (2 * W + 1);
     MD_CUDA_TRY(cudaMemsetAsync(hist_out, 0, nb * sizeof(int32_t), st));
     MD_CUDA_TRY(cudaMemsetAsync(overflow_out, 0, sizeof(int64_t), st));
-    return bin_launch(t0, t1, n, lx, W, hist_out, overflow_out, mom_out, scratch[dev], grid, st);
+    return bin_launch(t0, t1, n, lx, W, hist_out, overflow_out, mom_out, scratch, grid, st);
 }
