@@ -69,6 +69,7 @@ extern "C" {
 #define MD_MAX_DX 4        /* lattice spacings per system                   */
 #define MD_MAX_W 10        /* largest displacement window half-width        */
 #define MD_NBLK 32         /* error-bar blocks per histogram                */
+#define MD_MAX_REP 4096    /* replicas per batch                            */
 
 /* Parameters of one system (one replica of a batch).  Units: LJ (sigma,
  * eps, m, tau).  The sampling interval of slot k is Delta t_LG =
@@ -180,15 +181,23 @@ int md_step(md_system *s, int64_t nsteps);
  * entries are copied to shared memory (double buffered) before its forces
  * are computed, 2 = neighbours are read from global memory through L1,
  * 3 = as 2 with the register budget of full occupancy (8 CTAs of 256
- * threads per SM; FP32 only, in FP64 the same as 2) (0 = 1).  Results do
- * not depend on the shape: particle order, force
- * summation order and every reduction order are fixed by the data, not by
- * the launch.  Used by md_autotune. */
+ * threads per SM; FP32 only, in FP64 the same as 2) (0 = 1).
+ * staging 4 selects the shared-memory-resident engine instead (FP32 only):
+ * every replica is cut into slabs of whole MD-cell rows, each slab held in
+ * one CTA's shared memory (state and Verlet lists) for the whole md_step,
+ * the slabs of a replica exchanging their boundary rows through L2 and
+ * meeting at a bounded per-replica barrier once per step; block_threads and
+ * per_thread are ignored; MD_E_LIMIT if a replica fits no slab plan.
+ * Results do not depend on the shape or the engine: particle order, force
+ * summation order, every reduction order and the rebuild schedule (per
+ * replica) are fixed by the data, not by the launch; only the FP64 moment
+ * sums are grouped differently by the two engines (their last bits may
+ * differ).  Used by md_autotune. */
 int md_tune(md_system *s, int32_t block_threads, int32_t per_thread, int32_t staging);
 
 /* Autotuner: times md_step(steps_per_trial) twice for every launch shape
  * (block {256,128} x per_thread {1,2,4} x staging {1,2,3}; 3 skipped in
- * FP64) and keeps the
+ * FP64; then staging 4 for FP32 batches of >= 2 replicas) and keeps the
  * fastest; the choice is cached for the process by (precision, replicas,
  * particle count rounded up to a power of two, list capacity) and reused
  * without trials.  The trial steps are real MD steps: the system advances
@@ -196,6 +205,19 @@ int md_tune(md_system *s, int32_t block_threads, int32_t per_thread, int32_t sta
  * (host, may be NULL) receives {block_threads, per_thread, staging}.
  * Synchronises. */
 int md_autotune(md_system *s, int64_t steps_per_trial, int32_t *best3);
+
+/* Host-only dry run of the resident engine's plan (md_tune staging 4) for
+ * the replicas p[0 .. n_rep) on `grid` CTAs with smem_bytes of dynamic
+ * shared memory each (no GPU call; a project addition, no counterpart in
+ * the paper).  Each replica is cut into g slabs of whole MD-cell rows; the
+ * slabs are dealt to the CTAs.  jobs_out (host, [max_jobs][8]) receives per
+ * slab {replica, g, k, first row, end row, particle capacity, halo capacity,
+ * CTA of slab 0}, grouped by CTA in execution order; start_out (host,
+ * [grid + 1]) the first slab of each CTA; *makespan (may be NULL) the
+ * plan's estimated time in its cost units.  MD_E_LIMIT when a replica fits
+ * no plan or there are more than max_jobs slabs. */
+int md_resident_plan(const md_params *p, int32_t n_rep, int32_t grid, int64_t smem_bytes, int32_t *jobs_out,
+                     int32_t max_jobs, int32_t *start_out, double *makespan);
 
 /* Waits for the system's stream and returns the device status word (and
  * clears it). */
@@ -318,6 +340,17 @@ int mdlg_bin(const md_snapshot *t0, const md_snapshot *t1, int64_t n, int32_t lx
  * make that first call before any stream capture. */
 int mdlg_bin_noalloc(const md_snapshot *t0, const md_snapshot *t1, int64_t n, int32_t lx, int32_t W,
                      int32_t *hist_out, int64_t *overflow_out, double *mom_out, void *stream);
+
+/* ---- arithmetic peaks (measurement; no counterpart in the paper) -------- */
+
+/* Measured fused multiply-add throughput of the current GPU, FP32 (f64 = 0)
+ * or FP64 (f64 = 1): the full resident grid runs 8 independent FFMA / DFMA
+ * chains per thread for `iters` rounds (1 <= iters <= 2^32) after a short
+ * warm-up, timed with CUDA events on `stream`.  *flops_per_s (host)
+ * receives 2 flops per multiply-add over the elapsed time, *ms_out (host,
+ * may be NULL) the time.  The denominator of the FP64 MD path's roofline
+ * and of the shared-memory-resident FP32 path's.  Synchronises. */
+int mdlg_fma_peak(int32_t f64, int64_t iters, double *flops_per_s, double *ms_out, void *stream);
 
 /* ---- local MDLG fields (Sec. 2, Eqs. n_i and mdlg_evolution) ------------ */
 

@@ -25,7 +25,7 @@ int fail(int code, const char *fmt, ...);
 
 // Device status word values (a device-side failure sets one, the host reads
 // it at md_sync).
-enum DevStatus : int { DS_OK = 0, DS_TIMEOUT = 1, DS_SKIN = 2, DS_NONFINITE = 4, DS_NBR_OVERFLOW = 8 };
+enum DevStatus : int { DS_OK = 0, DS_TIMEOUT = 1, DS_SKIN = 2, DS_NONFINITE = 4, DS_NBR_OVERFLOW = 8, DS_CAPACITY = 16 };
 
 // ---------------------------------------------------------------- device memory order
 __device__ __forceinline__ unsigned ld_acquire_gpu(const unsigned *p) {

@@ -15,6 +15,7 @@
 #include "common.cuh"
 #include "equilibria.cuh"
 #include "md_kernels.cuh"
+#include "md_resident.cuh"
 
 namespace mdlg {
 
@@ -460,6 +461,15 @@ struct md_system {
     double *d_feq_par = nullptr;    // per replica mu2, a^2, lambda of the f_eq stage [nrep][4]
     long long *d_hist64 = nullptr;
     int32_t *d_nc_of_id = nullptr;
+    // resident engine (md_tune staging 4): plan, buffers, launch shape; the
+    // global engine's cell lists need a sort-only rebuild after its launches
+    int engine = 0;                   // 0 = k_md_persistent, 1 = k_md_resident
+    bool needs_sort = false;
+    std::vector<void *> res_allocs;
+    ResDev rd{};
+    int res_grid = 0;
+    size_t res_smem = 0;
+    int res_slabs = 0, res_max_g = 0;
 };
 
 namespace {
@@ -488,10 +498,238 @@ const void *persistent_fn(int prec, int block, int stage) {
                         : (const void *)k_md_persistent<float, 256, false>;
 }
 
+// Per-replica constants from the parameters (slot, cell and id bases are
+// set by the caller).
+RepDev make_rep(const md_params &q, int prec, int n_dx) {
+    RepDev R{};
+    R.nc = (int)std::floor(q.box_L / (q.rc + q.skin));
+    double h = q.box_L / R.nc;
+    if (prec == MD_FP32_CELLOFF) h = (double)(float)h;
+    R.h = h;
+    R.L = (double)R.nc * h;
+    R.n = (int)q.n;
+    R.cap = (int)((q.n + SLOT_PAD - 1) / SLOT_PAD * SLOT_PAD);
+    R.dt = q.dt;
+    R.hk = q.dt / (2.0 * q.mass);
+    R.rc2 = q.rc * q.rc;
+    R.eps = q.eps;
+    R.sig2 = q.sigma * q.sigma;
+    const double sc2 = q.sigma * q.sigma / (q.rc * q.rc), sc6 = sc2 * sc2 * sc2;
+    R.vshift = 4.0 * q.eps * (sc6 * sc6 - sc6);
+    R.mass = q.mass;
+    R.rv2 = (q.rc + q.skin) * (q.rc + q.skin);
+    R.half_skin = 0.5 * q.skin;
+    for (int d = 0; d < n_dx; ++d) {
+        R.lx[d] = q.lx[d];
+        R.dxl[d] = R.L / (double)q.lx[d];
+    }
+    R.hf = (float)h;
+    R.dtf = (float)R.dt;
+    R.hkf = (float)R.hk;
+    R.rc2f = (float)R.rc2;
+    R.epsf = (float)R.eps;
+    R.sig2f = (float)R.sig2;
+    R.rv2f = (float)R.rv2;
+    return R;
+}
+
+// ---- resident engine plan -------------------------------------------------
+// Cuts every replica into g slabs of whole MD-cell rows, the fewest that fit
+// one CTA's shared memory each with room to spare (particles 1.2x the
+// expected count of the largest slab plus 64, halo rows twice the mean row
+// population plus 64, list entries 1.8x the mean neighbour count within
+// rc + skin), then deals the slabs to `grid` CTAs by list scheduling: the
+// replicas in order of decreasing g and estimated time, each on the
+// contiguous CTA range that frees up first.  Every CTA runs its slabs in
+// order of their planned start, so the slabs of one replica meet in the
+// same order on all their CTAs (no cycle of waits).
+struct ResPlan {
+    std::vector<ResJob> jobs;        // by CTA, in execution order
+    std::vector<int32_t> start;      // [grid + 1]
+    int hmax = 0, slabs = 0, max_g = 0;
+    double makespan = 0.0;
+};
+
+static int round_up(long long v, int m) { return (int)((v + m - 1) / m * m); }
+
+int plan_resident(const std::vector<RepDev> &all, int grid, size_t avail, ResPlan &P) {
+    struct Rep {
+        int r, g, p_cap, h_cap;
+        double cost;
+    };
+    std::vector<Rep> reps;
+    for (int r = 0; r < (int)all.size(); ++r) {
+        const RepDev &R = all[r];
+        const double dens = (double)R.n / (R.L * R.L);
+        const double cbar = M_PI * R.rv2 * dens;
+        const double rowpop = (double)R.n / R.nc;
+        Rep best{r, 0, 0, 0, 0.0};
+        for (int g = 1; g <= 1024; ++g) {
+            if (g > 1 && (R.nc / g < 2 || g > R.cap / 32)) break;
+            const int rows = (R.nc + g - 1) / g;
+            if ((g == 1 ? R.nc : rows + 2) > RES_NCC) continue;
+            const double pmax = (double)R.n * rows / R.nc;
+            const double want = 1.2 * pmax + 64.0;
+            if (want > RES_PCAP) continue;
+            const int p_cap = std::min(RES_PCAP, round_up((long long)std::ceil(want), 32));
+            const int h_cap = g == 1 ? 0 : std::min(4096, round_up((long long)std::ceil(2.0 * rowpop + 64.0), 32));
+            if (p_cap + 2 * h_cap > (int)RES_IDX + 1) continue;   // 14-bit list indices
+            const long long e_need = (long long)std::ceil(1.8 * cbar * p_cap) + 256;
+            if (res_slab_bytes(p_cap, h_cap, (int)std::min<long long>(e_need, 1 << 30)) > avail) continue;
+            best = Rep{r, g, p_cap, h_cap, pmax * (40.0 + 14.0 * cbar) + (g > 1 ? 4000.0 : 0.0)};
+            break;
+        }
+        if (best.g == 0)
+            return fail(MD_E_LIMIT, "resident engine: replica %d (n = %d, %d cell rows) fits no slab plan", r, R.n,
+                        R.nc);
+        reps.push_back(best);
+    }
+    std::stable_sort(reps.begin(), reps.end(), [](const Rep &a, const Rep &b) {
+        return a.g != b.g ? a.g > b.g : a.cost > b.cost;
+    });
+    std::vector<double> free_at(grid, 0.0);
+    struct Placed {
+        double t;
+        ResJob j;
+    };
+    std::vector<std::vector<Placed>> per_cta(grid);
+    P.hmax = 32;
+    P.slabs = 0;
+    P.max_g = 0;
+    for (const Rep &q : reps) {
+        if (q.g > grid) return fail(MD_E_LIMIT, "resident engine: replica %d needs %d CTAs > %d", q.r, q.g, grid);
+        int c0 = 0;
+        double best_t = 1e300, best_idle = 1e300;
+        for (int c = 0; c + q.g <= grid; ++c) {
+            double t = 0.0;
+            for (int k = 0; k < q.g; ++k) t = std::max(t, free_at[c + k]);
+            double idle = 0.0;
+            for (int k = 0; k < q.g; ++k) idle += t - free_at[c + k];
+            if (t < best_t || (t == best_t && idle < best_idle)) {
+                best_t = t;
+                best_idle = idle;
+                c0 = c;
+            }
+        }
+        const RepDev &R = all[q.r];
+        for (int k = 0; k < q.g; ++k) {
+            ResJob j;
+            j.rep = q.r;
+            j.g = q.g;
+            j.k = k;
+            j.r0 = (int)((long long)k * R.nc / q.g);
+            j.r1 = (int)((long long)(k + 1) * R.nc / q.g);
+            j.p_cap = q.p_cap;
+            j.h_cap = q.h_cap;
+            j.cta0 = c0;
+            per_cta[c0 + k].push_back(Placed{best_t, j});
+            free_at[c0 + k] = best_t + q.cost;
+        }
+        P.hmax = std::max(P.hmax, q.h_cap);
+        P.slabs += q.g;
+        P.max_g = std::max(P.max_g, q.g);
+    }
+    P.jobs.clear();
+    P.start.assign(grid + 1, 0);
+    P.makespan = 0.0;
+    for (int c = 0; c < grid; ++c) {
+        std::stable_sort(per_cta[c].begin(), per_cta[c].end(),
+                         [](const Placed &a, const Placed &b) { return a.t < b.t; });
+        P.start[c] = (int)P.jobs.size();
+        for (const Placed &x : per_cta[c]) P.jobs.push_back(x.j);
+        P.makespan = std::max(P.makespan, free_at[c]);
+    }
+    P.start[grid] = (int)P.jobs.size();
+    return MD_OK;
+}
+
+void free_resident(md_system *s) {
+    for (void *p : s->res_allocs) cudaFree(p);
+    s->res_allocs.clear();
+    s->rd = ResDev{};
+    s->res_grid = 0;
+}
+
+int configure_resident(md_system *s) {
+    if (s->prec != MD_FP32_CELLOFF) return fail(MD_E_ARG, "the resident engine (staging 4) is FP32 only");
+    int optin = 0;
+    MD_CUDA_TRY(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, s->dev));
+    cudaFuncAttributes fa{};
+    MD_CUDA_TRY(cudaFuncGetAttributes(&fa, k_md_resident));
+    const size_t smem = (size_t)optin - fa.sharedSizeBytes;
+    const size_t hb = smem_hist_bytes(s->n_lg, s->n_dx, s->nb);
+    if (hb + 4096 > smem) return fail(MD_E_LIMIT, "resident engine: histograms leave no shared memory");
+    MD_CUDA_TRY(cudaFuncSetAttribute(k_md_resident, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    int occ = 0;
+    MD_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_md_resident, RES_THREADS, smem));
+    if (occ < 1) return fail(MD_E_CUDA, "resident kernel does not fit on an SM");
+    const int grid = s->nsm;
+    ResPlan P;
+    int rc = plan_resident(s->reps, grid, smem - hb, P);
+    if (rc) return rc;
+    MD_CUDA_TRY(cudaStreamSynchronize(s->st));   // no launch may still use the old buffers
+    free_resident(s);
+    ResDev &D = s->rd;
+    auto A = [&](void **ptr, size_t bytes) {
+        if (rc) return;
+        if (cudaMalloc(ptr, bytes ? bytes : 16) != cudaSuccess) {
+            *ptr = nullptr;
+            rc = fail(MD_E_NOMEM, "resident engine: cudaMalloc(%zu)", bytes);
+            return;
+        }
+        s->res_allocs.push_back(*ptr);
+    };
+    const size_t hm = (size_t)P.hmax;
+    A((void **)&D.jobs, sizeof(ResJob) * P.jobs.size());
+    A((void **)&D.job_start, sizeof(int32_t) * P.start.size());
+    A((void **)&D.halo_off, sizeof(float2) * grid * 4 * hm);
+    A((void **)&D.halo_ci, sizeof(uint2) * grid * 2 * hm);
+    A((void **)&D.halo_n, sizeof(int32_t) * grid * 2);
+    A((void **)&D.mig_a, sizeof(float4) * grid * 2 * hm);
+    A((void **)&D.mig_b, sizeof(uint2) * grid * 2 * hm);
+    A((void **)&D.mig_n, sizeof(int32_t) * grid * 2);
+    A((void **)&D.slab_n, sizeof(int32_t) * grid);
+    A((void **)&D.gbar, sizeof(unsigned) * 2 * (size_t)s->nrep);
+    if (rc) {
+        free_resident(s);
+        return rc;
+    }
+    D.hmax = P.hmax;
+    D.smem_bytes = (int)smem;
+    MD_CUDA_TRY(cudaMemcpyAsync((void *)D.jobs, P.jobs.data(), sizeof(ResJob) * P.jobs.size(),
+                                cudaMemcpyHostToDevice, s->st));
+    MD_CUDA_TRY(cudaMemcpyAsync((void *)D.job_start, P.start.data(), sizeof(int32_t) * P.start.size(),
+                                cudaMemcpyHostToDevice, s->st));
+    MD_CUDA_TRY(cudaMemsetAsync(D.gbar, 0, sizeof(unsigned) * 2 * (size_t)s->nrep, s->st));
+    s->res_grid = grid;
+    s->res_smem = smem;
+    s->res_slabs = P.slabs;
+    s->res_max_g = P.max_g;
+    s->engine = 1;   // the global engine keeps its own launch shape for its other uses
+    return MD_OK;
+}
+
+int launch_resident(md_system *s, long long nsteps) {
+    for (long long done = 0; done < nsteps;) {
+        long long step0 = s->step + done;
+        long long n = std::min(RES_MAX_STEPS, nsteps - done);
+        int phase = done ? 1 : s->phase_half;
+        void *args[] = {&s->sd, &s->rd, &step0, &n, &phase};
+        MD_CUDA_TRY(cudaLaunchCooperativeKernel((const void *)k_md_resident, dim3(s->res_grid), dim3(RES_THREADS),
+                                                args, s->res_smem, s->st));
+        k_res_flip<<<1, 1, 0, s->st>>>(s->d_ctl);
+        MD_CUDA_TRY(cudaGetLastError());
+        done += n;
+    }
+    s->needs_sort = true;
+    return MD_OK;
+}
+
 int configure_launch(md_system *s, int block, int ppt, int stage) {
+    if (stage == 4) return configure_resident(s);
     if (block != 128 && block != 256) return fail(MD_E_ARG, "block_threads must be 128 or 256");
     if (ppt < 1 || ppt > 8) return fail(MD_E_ARG, "per_thread must be in [1, 8]");
-    if (stage < 1 || stage > 3) return fail(MD_E_ARG, "staging must be 1, 2 or 3");
+    if (stage < 1 || stage > 3) return fail(MD_E_ARG, "staging must be 1, 2, 3 or 4");
     const void *fn = persistent_fn(s->prec, block, stage);
     const int chunk = ppt * block;
     // chunk table: ppt*block consecutive slots of one replica
@@ -503,8 +741,9 @@ int configure_launch(md_system *s, int block, int ppt, int stage) {
     }
     if ((long long)ch.size() > s->chunk_cap) return fail(MD_E_LIMIT, "chunk table overflow");
     const long long nch = (long long)ch.size();
-    const size_t smem = s->prec == MD_FP64 ? smem_bytes<double>(s->n_lg, s->n_dx, s->nb, chunk, stage == 1)
-                                           : smem_bytes<float>(s->n_lg, s->n_dx, s->nb, chunk, stage == 1);
+    const size_t smem = s->prec == MD_FP64
+                            ? smem_bytes<double>(s->n_lg, s->n_dx, s->nb, chunk, stage == 1, s->nrep)
+                            : smem_bytes<float>(s->n_lg, s->n_dx, s->nb, chunk, stage == 1, s->nrep);
     if (smem > 227 * 1024) return fail(MD_E_LIMIT, "shared memory per CTA exceeds 227 KB");
     MD_CUDA_TRY(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     int occ = 0;
@@ -554,10 +793,28 @@ int configure_launch(md_system *s, int block, int ppt, int stage) {
     s->sd.ppt = ppt;
     s->sd.stage = stage == 1;
     s->stage = stage;
+    s->engine = 0;
     return MD_OK;
 }
 
+int launch_persistent(md_system *s, long long nsteps, int force_rebuild);
+
+// The global engine's invariants (slots sorted by cell, by id inside a cell,
+// cell_start, Verlet lists) after a resident launch: a sort-only rebuild,
+// which moves no particle's cell and changes no value.
+int ensure_sorted(md_system *s) {
+    if (!s->needs_sort) return MD_OK;
+    s->needs_sort = false;
+    return launch_persistent(s, 0, RB_NONE);
+}
+
 int launch_persistent(md_system *s, long long nsteps, int force_rebuild) {
+    if (force_rebuild != RB_ALL) {
+        int rc = ensure_sorted(s);
+        if (rc) return rc;
+    } else {
+        s->needs_sort = false;
+    }
     const void *fn = persistent_fn(s->prec, s->block, s->stage);
     long long step0 = s->step;
     int phase = s->phase_half;
@@ -568,6 +825,8 @@ int launch_persistent(md_system *s, long long nsteps, int force_rebuild) {
 
 int status_to_code(int ds) {
     if (ds & DS_TIMEOUT) return fail(MD_E_TIMEOUT, "device barrier wait timed out");
+    if (ds & DS_CAPACITY)
+        return fail(MD_E_LIMIT, "resident engine: a slab outgrew its planned capacity (state undefined)");
     if (ds & DS_NONFINITE) return fail(MD_E_NONFINITE, "non-finite position encountered");
     if (ds & DS_SKIN) return fail(MD_E_SKIN, "a particle moved more than one cell in one step");
     if (ds & DS_NBR_OVERFLOW)
@@ -584,6 +843,8 @@ int sync_status(md_system *s) {
         // a wait that gave up leaves the arrival count behind; no kernel of
         // the system runs now, so it is cleared for the next launch
         if (ds & DS_TIMEOUT) MD_CUDA_TRY(cudaMemset(&s->d_ctl->bar_count, 0, sizeof(unsigned)));
+        if ((ds & (DS_TIMEOUT | DS_CAPACITY)) && s->rd.gbar)
+            MD_CUDA_TRY(cudaMemset(s->rd.gbar, 0, sizeof(unsigned) * 2 * (size_t)s->nrep));
         return status_to_code(ds);
     }
     return MD_OK;
@@ -666,6 +927,8 @@ int upload_state(md_system *s, const double *x, const double *y, const double *v
 
 // Runs the observation kernel; completes the half kick when needed.
 int observe(md_system *s, ObsArgs a) {
+    int rc = ensure_sorted(s);
+    if (rc) return rc;
     a.complete = s->phase_half;
     const int nthr = 256;
     const int nblk = s->nslots / nthr;
@@ -695,6 +958,7 @@ extern "C" {
 int md_init_batch(const md_params *p, int32_t n_rep, const double *x, const double *y,
                   const double *vx, const double *vy, void *stream, md_system **out) {
     if (!p || !out || n_rep < 1) return fail(MD_E_ARG, "md_init_batch: bad arguments");
+    if (n_rep > MD_MAX_REP) return fail(MD_E_LIMIT, "md_init_batch: more than %d replicas", MD_MAX_REP);
     *out = nullptr;
     for (int r = 0; r < n_rep; ++r) {
         int rc = check_params(&p[r], r, r ? &p[0] : nullptr);
@@ -714,38 +978,10 @@ int md_init_batch(const md_params *p, int32_t n_rep, const double *x, const doub
     long long pbase = 0, cbase = 0, ibase = 0;
     for (int r = 0; r < n_rep; ++r) {
         const md_params &q = p[r];
-        RepDev R{};
-        R.nc = (int)std::floor(q.box_L / (q.rc + q.skin));
-        double h = q.box_L / R.nc;
-        if (s->prec == MD_FP32_CELLOFF) h = (double)(float)h;
-        R.h = h;
-        R.L = (double)R.nc * h;
-        R.n = (int)q.n;
-        R.cap = (int)((q.n + SLOT_PAD - 1) / SLOT_PAD * SLOT_PAD);
+        RepDev R = make_rep(q, s->prec, s->n_dx);
         R.pbase = (int)pbase;
         R.cbase = (int)cbase;
         R.ibase = (int)ibase;
-        R.dt = q.dt;
-        R.hk = q.dt / (2.0 * q.mass);
-        R.rc2 = q.rc * q.rc;
-        R.eps = q.eps;
-        R.sig2 = q.sigma * q.sigma;
-        const double sc2 = q.sigma * q.sigma / (q.rc * q.rc), sc6 = sc2 * sc2 * sc2;
-        R.vshift = 4.0 * q.eps * (sc6 * sc6 - sc6);
-        R.mass = q.mass;
-        R.rv2 = (q.rc + q.skin) * (q.rc + q.skin);
-        R.half_skin = 0.5 * q.skin;
-        for (int d = 0; d < s->n_dx; ++d) {
-            R.lx[d] = q.lx[d];
-            R.dxl[d] = R.L / (double)q.lx[d];
-        }
-        R.hf = (float)h;
-        R.dtf = (float)R.dt;
-        R.hkf = (float)R.hk;
-        R.rc2f = (float)R.rc2;
-        R.epsf = (float)R.eps;
-        R.sig2f = (float)R.sig2;
-        R.rv2f = (float)R.rv2;
         s->reps.push_back(R);
         pbase += R.cap;
         cbase += (long long)R.nc * R.nc + 1;
@@ -808,6 +1044,8 @@ int md_init_batch(const md_params *p, int32_t n_rep, const double *x, const doub
     ALLOC(S.hist, sizeof(int32_t) * nhist);
     ALLOC(S.ovf, sizeof(unsigned long long) * n_rep * nlg * s->n_dx);
     ALLOC(S.mom, sizeof(double) * ngr * nlg * 2);
+    ALLOC(S.vmax_rep, sizeof(unsigned) * 3 * (size_t)n_rep);
+    ALLOC(S.disp_rep, sizeof(double) * (size_t)n_rep);
     ALLOC(s->d_epart, sizeof(double) * ngr * 4);
     ALLOC(s->d_small, sizeof(double) * (2 * s->nb + 16));
     ALLOC(s->d_feq_part, sizeof(double) * (size_t)n_rep * FEQB_SPLIT * s->nb);
@@ -851,6 +1089,8 @@ int md_init_batch(const md_params *p, int32_t n_rep, const double *x, const doub
     tryc(cudaMemsetAsync(S.hist, 0, sizeof(int32_t) * nhist, s->st));
     tryc(cudaMemsetAsync(S.ovf, 0, sizeof(unsigned long long) * n_rep * nlg * s->n_dx, s->st));
     tryc(cudaMemsetAsync(S.mom, 0, sizeof(double) * ngr * nlg * 2, s->st));
+    tryc(cudaMemsetAsync(S.vmax_rep, 0, sizeof(unsigned) * 3 * (size_t)n_rep, s->st));
+    tryc(cudaMemsetAsync(S.disp_rep, 0, sizeof(double) * (size_t)n_rep, s->st));
     tryc(cudaMemsetAsync(S.snap_cell, 0, sizeof(uint32_t) * nlg * s->ntot, s->st));
     tryc(cudaMemsetAsync(S.snap_off, 0, vsz * nlg * s->ntot, s->st));
     if (rc == MD_OK) {
@@ -867,6 +1107,34 @@ int md_init_batch(const md_params *p, int32_t n_rep, const double *x, const doub
     return MD_OK;
 }
 
+int md_resident_plan(const md_params *p, int32_t n_rep, int32_t grid, int64_t smem_bytes, int32_t *jobs_out,
+                     int32_t max_jobs, int32_t *start_out, double *makespan) {
+    if (!p || n_rep < 1 || n_rep > MD_MAX_REP || grid < 1 || smem_bytes < 4096 || !jobs_out || !start_out ||
+        max_jobs < 0)
+        return fail(MD_E_ARG, "md_resident_plan: bad arguments");
+    std::vector<RepDev> reps;
+    for (int r = 0; r < n_rep; ++r) {
+        int rc = check_params(&p[r], r, r ? &p[0] : nullptr);
+        if (rc) return rc;
+        reps.push_back(make_rep(p[r], p[0].precision, p[0].n_dx));
+    }
+    const int nb = (2 * p[0].W + 1) * (2 * p[0].W + 1);
+    const size_t hb = smem_hist_bytes(p[0].n_lg, p[0].n_dx, nb);
+    if ((size_t)smem_bytes <= hb) return fail(MD_E_LIMIT, "md_resident_plan: no shared memory left");
+    ResPlan P;
+    int rc = plan_resident(reps, grid, (size_t)smem_bytes - hb, P);
+    if (rc) return rc;
+    if ((int)P.jobs.size() > max_jobs) return fail(MD_E_LIMIT, "md_resident_plan: %d slabs > max_jobs", (int)P.jobs.size());
+    for (size_t j = 0; j < P.jobs.size(); ++j) {
+        const ResJob &J = P.jobs[j];
+        const int32_t v[8] = {J.rep, J.g, J.k, J.r0, J.r1, J.p_cap, J.h_cap, J.cta0};
+        std::memcpy(jobs_out + 8 * j, v, sizeof(v));
+    }
+    std::memcpy(start_out, P.start.data(), sizeof(int32_t) * P.start.size());
+    if (makespan) *makespan = P.makespan;
+    return MD_OK;
+}
+
 int md_init(const md_params *p, const double *x, const double *y, const double *vx,
             const double *vy, void *stream, md_system **out) {
     return md_init_batch(p, 1, x, y, vx, vy, stream, out);
@@ -875,6 +1143,7 @@ int md_init(const md_params *p, const double *x, const double *y, const double *
 void md_destroy(md_system *s) {
     if (!s) return;
     if (s->st) cudaStreamSynchronize(s->st);
+    free_resident(s);
     for (void *p : s->allocs) cudaFree(p);
     delete s;
 }
@@ -882,7 +1151,7 @@ void md_destroy(md_system *s) {
 int md_step(md_system *s, int64_t nsteps) {
     if (!s || nsteps < 0) return fail(MD_E_ARG, "md_step: bad arguments");
     if (nsteps == 0) return MD_OK;
-    int rc = launch_persistent(s, nsteps, 0);
+    int rc = s->engine == 1 ? launch_resident(s, nsteps) : launch_persistent(s, nsteps, 0);
     if (rc) return rc;
     s->step += nsteps;
     s->phase_half = 1;
@@ -905,10 +1174,12 @@ int md_barrier_selftest(md_system *s, double limit_s) {
     const uint64_t keep = s->sd.timeout_ns;
     s->sd.timeout_ns = (uint64_t)(limit_s * 1e9);
     s->sd.dbg_leave_cta = 0;
-    rc = md_step(s, 1);
+    rc = launch_persistent(s, 1, 0);   // the global engine's grid barrier
     s->sd.dbg_leave_cta = -1;
     s->sd.timeout_ns = keep;
     if (rc) return rc;
+    s->step += 1;
+    s->phase_half = 1;
     return sync_status(s);
 }
 
@@ -1206,6 +1477,24 @@ int md_autotune(md_system *s, int64_t steps_per_trial, int32_t *best3) {
                     bs = st;
                 }
             }
+    // the shared-memory-resident engine (batched FP32 ensembles)
+    if (rc == MD_OK && s->prec == MD_FP32_CELLOFF && s->nrep >= 2 && configure_launch(s, 256, 1, 4) == MD_OK) {
+        rc = md_step(s, steps_per_trial);
+        if (rc == MD_OK) {
+            cudaEventRecord(e0, s->st);
+            rc = md_step(s, steps_per_trial);
+            cudaEventRecord(e1, s->st);
+            cudaEventSynchronize(e1);
+            float ms = 0.0f;
+            cudaEventElapsedTime(&ms, e0, e1);
+            if (rc == MD_OK && ms < best_ms) {
+                best_ms = ms;
+                bb = 256;
+                bp = 1;
+                bs = 4;
+            }
+        }
+    }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     if (rc) return rc;

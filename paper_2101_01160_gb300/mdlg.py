@@ -22,7 +22,7 @@ MD_OK = 0
 MD_E_ARG, MD_E_CUDA, MD_E_TIMEOUT, MD_E_SKIN, MD_E_NONFINITE, MD_E_DOMAIN, MD_E_NOMEM, MD_E_LIMIT = \
     -1, -2, -3, -4, -5, -6, -7, -8
 MD_FP64, MD_FP32_CELLOFF = 0, 1
-MD_MAX_LG, MD_MAX_DX, MD_MAX_W, MD_NBLK = 8, 4, 10, 32
+MD_MAX_LG, MD_MAX_DX, MD_MAX_W, MD_NBLK, MD_MAX_REP = 8, 4, 10, 32, 4096
 
 
 class MDError(RuntimeError):
@@ -73,6 +73,7 @@ _SIGS = {
     "md_step": ([P, C.c_int64], C.c_int),
     "md_sync": ([P], C.c_int),
     "md_barrier_selftest": ([P, C.c_double], C.c_int),
+    "md_resident_plan": ([C.POINTER(md_params), C.c_int32, C.c_int32, C.c_int64, P, C.c_int32, P, P], C.c_int),
     "md_tune": ([P, C.c_int32, C.c_int32, C.c_int32], C.c_int),
     "md_autotune": ([P, C.c_int64, P], C.c_int),
     "md_info": ([P, C.POINTER(md_info_t)], C.c_int),
@@ -104,6 +105,7 @@ _SIGS = {
     "feq_wsg": ([C.c_double, C.c_double, C.c_double, C.c_double, C.c_int32, P, P], C.c_int),
     "feq_compare": ([P, P, C.c_int32, P, P], C.c_int),
     "md_last_error": ([], C.c_char_p),
+    "mdlg_fma_peak": ([C.c_int32, C.c_int64, P, P, P], C.c_int),
     "mlp_create": ([C.c_int32, C.c_int32, C.c_int32, P, P, P, C.POINTER(P)], C.c_int),
     "mlp_destroy": ([P], None),
     "mlp_param_count": ([P], C.c_int64),
@@ -295,6 +297,20 @@ class System:
         return Pm, se, st
 
 
+def resident_plan(params, grid, smem_bytes, max_jobs=1 << 16):
+    """Host-only dry run of the resident engine's plan (md_resident_plan):
+    (jobs int32 [n, 8] = replica, g, k, r0, r1, p_cap, h_cap, cta0; grouped by
+    CTA in execution order, start int32 [grid + 1], makespan)."""
+    params = list(params)
+    arr = (md_params * len(params))(*params)
+    jobs = np.zeros((max_jobs, 8), np.int32)
+    start = np.zeros(grid + 1, np.int32)
+    ms = C.c_double()
+    _check(load().md_resident_plan(arr, len(params), int(grid), int(smem_bytes), _ptr(jobs), max_jobs,
+                                   _ptr(start), C.byref(ms)))
+    return jobs[:start[-1]].copy(), start, ms.value
+
+
 FEQB_STATS = 16
 FEQB_FIELDS = ("mu2", "mu4", "a2", "lambda", "maxabs_g", "kl_g", "maxabs_wsg", "kl_wsg",
                "n_windows", "n_samples", "n_overflow", "dx_eff", "lambda_status", "sum_p")
@@ -483,6 +499,14 @@ def feq_compare(R, Q, stream=None):
     out = torch.empty(3, dtype=torch.float64, device="cuda")
     _check(load().feq_compare(_ptr(R), _ptr(Q), R.numel(), _ptr(out), _stream(stream)))
     return out
+
+
+def fma_peak(f64, iters=1 << 16, stream=None):
+    """Measured FMA throughput (flop/s) and the timed launch's ms."""
+    f = C.c_double()
+    ms = C.c_double()
+    _check(load().mdlg_fma_peak(int(f64), int(iters), C.byref(f), C.byref(ms), _stream(stream)))
+    return f.value, ms.value
 
 
 # ---------------------------------------------------------------- surrogate
