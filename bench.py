@@ -292,7 +292,10 @@ def _time_local_fields(mdlg, torch, reps=20):
 
 
 def run_profile_case(args):
-    """Small cases for ncu captures (not a bench line): md64 = the first 64
+    """Small cases for ncu captures (not a bench line): res16 = the first 16
+    replicas of the batched ensemble (about 360k particles) on the
+    shared-memory-resident engine, one 400-step launch then three 100-step
+    launches; md64 = the first 64
     replicas of the batched ensemble (about 1.4M particles, > L2), fixed
     launch shape (256 threads, 1 chunk per thread, global staging with the
     full-occupancy register budget, as the autotuner picks for the bench), two
@@ -306,7 +309,19 @@ def run_profile_case(args):
     from paper_2101_01160_gb300 import mdlg
 
     mdlg.load()
-    if args.profile_case == "md64":
+    if args.profile_case == "res16":
+        ens = ensemble(reps=range(16))
+        cat = [np.concatenate([getattr(e[4], f) for e in ens]) for f in ("x", "y", "vx", "vy")]
+        s = mdlg.System(_ens_params(mdlg, ens, mdlg.MD_FP32_CELLOFF), *cat)
+        s.tune(0, 0, 4)
+        s.step(MD_PER_STEP)
+        for _ in range(3):
+            s.step(100)
+        s.sync()
+        print(json.dumps({"profile_case": "res16", "n_particles": int(sum(e[0] for e in ens)),
+                          "rebuilds": int(s.info().n_rebuilds)}))
+        s.close()
+    elif args.profile_case == "md64":
         ens = ensemble(reps=range(64))
         cat = [np.concatenate([getattr(e[4], f) for e in ens]) for f in ("x", "y", "vx", "vy")]
         s = mdlg.System(_ens_params(mdlg, ens, mdlg.MD_FP32_CELLOFF), *cat)
@@ -528,7 +543,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-variants", action="store_true")
-    ap.add_argument("--profile-case", choices=["md64", "mlp", "disp", "local"], default=None,
+    ap.add_argument("--profile-case", choices=["md64", "res16", "mlp", "disp", "local"], default=None,
                     help="run a small case for ncu captures instead of the bench")
     args = ap.parse_args()
     if args.profile_case:

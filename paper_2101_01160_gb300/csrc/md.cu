@@ -742,8 +742,8 @@ int configure_launch(md_system *s, int block, int ppt, int stage) {
     if ((long long)ch.size() > s->chunk_cap) return fail(MD_E_LIMIT, "chunk table overflow");
     const long long nch = (long long)ch.size();
     const size_t smem = s->prec == MD_FP64
-                            ? smem_bytes<double>(s->n_lg, s->n_dx, s->nb, chunk, stage == 1, s->nrep)
-                            : smem_bytes<float>(s->n_lg, s->n_dx, s->nb, chunk, stage == 1, s->nrep);
+                            ? smem_bytes<double>(s->n_lg, s->n_dx, s->nb, chunk, stage == 1)
+                            : smem_bytes<float>(s->n_lg, s->n_dx, s->nb, chunk, stage == 1);
     if (smem > 227 * 1024) return fail(MD_E_LIMIT, "shared memory per CTA exceeds 227 KB");
     MD_CUDA_TRY(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     int occ = 0;

@@ -60,6 +60,8 @@ struct Control {
     int set, cur;
     int pad0;
     long long n_rebuilds;
+    unsigned vmax[3];     // global engine: per-step max |v| dt / half_skin (float bits), by step mod 3
+    unsigned pad1;
 };
 
 // Everything the kernels need, passed by value.
@@ -88,8 +90,9 @@ struct SysDev {
     unsigned long long *ovf;    // [nrep][n_lg][n_dx]
     double *mom;                // [nslots/32][n_lg][2]
     // per replica: the step's largest |v| dt / (skin/2) (float bits) by step
-    // mod 3, and the bound on any displacement since the replica's cells
-    // were last made canonical, in half skins (kept between launches)
+    // mod 3 (resident engine), and a bound on any displacement since the
+    // replica's cells were last made canonical, in half skins (kept between
+    // launches; the global engine keeps one bound for all, their maximum)
     unsigned *vmax_rep;         // [nrep][3]
     double *disp_rep;           // [nrep]
     long long ntot;
@@ -428,23 +431,19 @@ __device__ __forceinline__ void lj_list(const SysDev &S, const RepDev &R, const 
 }
 
 // ---------------------------------------------------------------- rebuild
-// Replicas whose displacement bound has reached half the skin (or all / none
-// of them, by `mode`) get canonical cells: each particle moves to the MD cell
-// its offset now lies in, the offset re-expressed from that cell's corner.
-// The others keep their cells.  Then a counting sort of all particles by
-// cell, particles inside one cell ordered by id, so the order -- and
-// therefore every force sum -- is reproducible and independent of the launch
-// shape; then the neighbour lists of every replica.  Six grid barriers.
-// Padding slots keep perm = -1 (set at creation).
-enum RebuildMode { RB_DUE = 0, RB_ALL = 1, RB_NONE = 2 };
-
-__device__ __forceinline__ bool rebuild_canon(int mode, const double *s_disp, int rep) {
-    return mode == RB_ALL || (mode == RB_DUE && s_disp[rep] >= 1.0);
-}
+// With mode RB_ALL every particle gets its canonical cell (the MD cell its
+// offset now lies in, the offset re-expressed from that cell's corner); with
+// RB_NONE every particle keeps its cell (a sort of a state written in
+// another order).  Then a counting sort of all particles by cell, particles
+// inside one cell ordered by id, so the order -- and therefore every force
+// sum -- is reproducible and independent of the launch shape; then the
+// neighbour lists.  Six grid barriers.  Padding slots keep perm = -1 (set at
+// creation).
+enum RebuildMode { RB_ALL = 1, RB_NONE = 2 };
 
 template <typename T, int BLOCK>
 __device__ bool rebuild(const SysDev &S, int &set, int &cur, unsigned &gen, int nloc,
-                        ChunkDesc *s_desc, int mode, const double *s_disp) {
+                        ChunkDesc *s_desc, int mode) {
     using V = typename V2<T>::type;
     Control *C = S.ctl;
     const GridBarrier bar{&C->bar_count, &C->bar_gen, &C->status};
@@ -456,7 +455,7 @@ __device__ bool rebuild(const SysDev &S, int &set, int &cur, unsigned &gen, int 
         const int4 cd = S.chunks[own_chunk(i)];
         const RepDev &R = S.reps[cd.x];
         const T h = rd<T>(R.h, R.hf);
-        const bool canon = rebuild_canon(mode, s_disp, cd.x);
+        const bool canon = mode == RB_ALL;
         for (int slot = cd.y + tid; slot < cd.z; slot += BLOCK) {
             const V o = pos[slot];
             const uint32_t cpk = cell[slot];
@@ -568,7 +567,7 @@ __device__ bool rebuild(const SysDev &S, int &set, int &cur, unsigned &gen, int 
             const int4 cd = S.chunks[own_chunk(i)];
             const RepDev &R = S.reps[cd.x];
             const T h = rd<T>(R.h, R.hf);
-            const bool canon = rebuild_canon(mode, s_disp, cd.x);
+            const bool canon = mode == RB_ALL;
             for (int slot = cd.y + tid; slot < cd.z; slot += BLOCK) {
                 const int old = S.perm[slot];
                 V o = pos[old];
@@ -706,33 +705,11 @@ __device__ inline Stage<T> stage_at(unsigned char *p, int chunk) {
     return B;
 }
 template <typename T>
-__host__ __device__ inline size_t smem_bytes(int n_lg, int n_dx, int nb, int chunk, bool staged,
-                                             int nrep) {
+__host__ __device__ inline size_t smem_bytes(int n_lg, int n_dx, int nb, int chunk, bool staged) {
     // the two staging buffers exist only when chunks are staged in shared
-    // memory; without them more CTAs fit on an SM; last, every replica's
-    // displacement bound
+    // memory; without them more CTAs fit on an SM
     return smem_hist_bytes(n_lg, n_dx, nb) + align16(MAX_CPC * sizeof(ChunkDesc)) +
-           (staged ? 2 * stage_bytes<T>(chunk) : 0) + align16((size_t)nrep * sizeof(double));
-}
-
-// Largest |v| dt / (skin/2) of one chunk of replica rep over the CTA,
-// merged into the replica's maximum of step s; vm is reset.  sv: two
-// buffers of BLOCK/32 floats used by alternate calls (parity), so that a
-// warp racing ahead into the next chunk cannot overwrite a value thread 0
-// has not read yet.
-template <int BLOCK>
-__device__ __forceinline__ void chunk_vmax(const SysDev &S, float &vm, int rep, long long s, float *sv,
-                                           int parity) {
-    for (int o = 16; o > 0; o >>= 1) vm = fmaxf(vm, __shfl_xor_sync(0xffffffffu, vm, o));
-    float *b = sv + parity * (BLOCK / 32);
-    if ((threadIdx.x & 31) == 0) b[threadIdx.x >> 5] = vm;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        float m = 0.0f;
-        for (int w = 0; w < BLOCK / 32; ++w) m = fmaxf(m, b[w]);
-        atomicMax(&S.vmax_rep[(long long)rep * 3 + s % 3], __float_as_uint(m));   // non-negative floats order as uints
-    }
-    vm = 0.0f;
+           (staged ? 2 * stage_bytes<T>(chunk) : 0);
 }
 
 // Records the force of one slot by particle id (md_step_forces only).
@@ -777,17 +754,16 @@ __device__ __forceinline__ void kick_drift(const RepDev &R, typename V2<T>::type
 //   force pass -- per slot: force F_s from the neighbour list; v += (dt/2m) F
 //     twice (the first kick completes the previous step unless velocities are
 //     at an integer step); off += dt v into the other position buffer; the
-//     largest |v| dt of each replica's particles is reduced into that
-//     replica's maximum for the step;
-//   grid barrier; every CTA adds each replica's maximum to its copy of the
-//     replica's displacement bound (the same sums in every CTA);
+//     largest |v| dt of the step is reduced grid-wide;
+//   grid barrier; every CTA adds it to the same displacement bound;
 //   sampling pass (steps t = n_equil + m*lg_every[k] only) -- bin each new
 //     position against its snapshot (Eq. n_i) and replace the snapshot;
-//   rebuild once the bound of any replica reaches half the skin: that
-//     replica's particles get canonical cells (until then no pair of it can
-//     have come within rc without being listed), every replica gets a fresh
-//     sort and lists.  The rebuild rule is per replica, so a replica's
-//     trajectory does not depend on the other replicas of the batch.
+//   rebuild (canonical cells, cell list + neighbour lists) once the
+//     accumulated bound on displacements since the last rebuild reaches half
+//     the skin: until then no pair can have come within rc without being
+//     listed.  One bound for the batch, so every replica is rebuilt together
+//     (one sort, six grid barriers); for a single replica this is the rule
+//     of the resident engine, which keeps one bound per replica.
 // CTAs per SM the register allocation is sized for: half occupancy (64
 // registers), or with DENSE full occupancy (32 registers: the spills cost
 // less than the extra latency hiding gains on large ensembles, whose
@@ -808,10 +784,10 @@ __global__ void __launch_bounds__(BLOCK, md_min_ctas(BLOCK, DENSE)) k_md_persist
     ChunkDesc *s_desc = reinterpret_cast<ChunkDesc *>(smem + hb);
     unsigned char *stg = smem + hb + align16(MAX_CPC * sizeof(ChunkDesc));
     const Stage<T> B0 = stage_at<T>(stg, chunk), B1 = stage_at<T>(stg + stage_bytes<T>(chunk), chunk);
-    double *s_disp = reinterpret_cast<double *>(stg + (S.stage ? 2 * stage_bytes<T>(chunk) : 0));
     __shared__ unsigned s_due;
     __shared__ long long s_win[MD_MAX_LG];
-    __shared__ float s_vmax[2 * (BLOCK / 32)];
+    __shared__ float s_vmax[BLOCK / 32];
+    __shared__ double s_dmax[BLOCK / 32];
     Control *C = S.ctl;
     const GridBarrier bar{&C->bar_count, &C->bar_gen, &C->status};
     const int tid = threadIdx.x, lane = tid & 31;
@@ -821,22 +797,28 @@ __global__ void __launch_bounds__(BLOCK, md_min_ctas(BLOCK, DENSE)) k_md_persist
     const int nloc = own_chunks(S.nchunks);
     const int per_lg = S.n_dx * S.nb;
     for (int e = tid; e < S.n_lg * per_lg; e += BLOCK) sh_hist[e] = 0;
-    // every CTA keeps the same copy of every replica's displacement bound
-    for (int r = tid; r < S.nrep; r += BLOCK) s_disp[r] = S.disp_rep[r];
-    __syncthreads();
+    // one bound for the whole batch: the largest of the replicas' bounds (a
+    // resident launch may have left them different)
+    double disp = 0.0;
+    {
+        double m = 0.0;
+        for (int r = tid; r < S.nrep; r += BLOCK) m = fmax(m, S.disp_rep[r]);
+        for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
+        if (lane == 0) s_dmax[tid >> 5] = m;
+        __syncthreads();
+        for (int w = 0; w < BLOCK / 32; ++w) disp = fmax(disp, s_dmax[w]);
+    }
 
     if (force_rebuild) {
-        // RB_ALL: canonical cells for every replica (a new state); RB_NONE:
-        // sort and lists without moving any particle's cell
-        if (!rebuild<T, BLOCK>(S, set, cur, gen, nloc, s_desc, force_rebuild, s_disp)) return;
-        if (force_rebuild == RB_ALL)
-            for (int r = tid; r < S.nrep; r += BLOCK) s_disp[r] = 0.0;
+        // RB_ALL: canonical cells (a new state); RB_NONE: sort and lists of a
+        // state written in another order, no particle's cell moved
+        if (!rebuild<T, BLOCK>(S, set, cur, gen, nloc, s_desc, force_rebuild)) return;
+        if (force_rebuild == RB_ALL) disp = 0.0;
     } else {
         for (int i = tid; i < nloc; i += BLOCK)
             s_desc[i] = make_desc(S, S.cell[set], own_chunk(i), WinParts<T>::value);
     }
     __syncthreads();
-    int vpar = 0;
     for (long long it = 0; it < nsteps; ++it) {
         const long long s = step0 + it;
         if (tid == 0) {
@@ -851,14 +833,13 @@ __global__ void __launch_bounds__(BLOCK, md_min_ctas(BLOCK, DENSE)) k_md_persist
                 }
             }
             s_due = due;
+            if (blockIdx.x == 0) C->vmax[(s + 1) % 3] = 0u;
         }
-        if (blockIdx.x == 0)
-            for (int r = tid; r < S.nrep; r += BLOCK) S.vmax_rep[(long long)r * 3 + (s + 1) % 3] = 0u;
         const bool first = (it == 0) ? (phase_half == 0) : false;
         const V *pin = static_cast<const V *>(S.pos[set][cur]);
         V *pout = static_cast<V *>(S.pos[set][cur ^ 1]);
         V *vel = static_cast<V *>(S.vel[set]);
-        float vm = 0.0f;   // largest |v| dt / (skin/2) of the current chunk
+        float vm = 0.0f;   // largest |v| dt / (skin/2) of this CTA's particles
         bool bad = false;
         // ---- force pass
         if (S.stage) {
@@ -889,12 +870,11 @@ __global__ void __launch_bounds__(BLOCK, md_min_ctas(BLOCK, DENSE)) k_md_persist
                     kick_drift<T>(R, oi, B.vel[li], fx, fy, hk, dt, first, vscale, pout, vel, slot, vm,
                                   bad);
                 }
-                chunk_vmax<BLOCK>(S, vm, d.rep, s, s_vmax, vpar);   // its sync also frees this buffer
-                vpar ^= 1;
+                __syncthreads();   // this buffer is refilled for chunk i+2
             }
             cp_async_wait<0>();
         } else {
-            // neighbours straight from global memory (L1/L2)
+            // neighbours straight from global memory (L1/L2); no CTA-wide sync
             ChunkDesc none{};
             for (int i = 0; i < nloc; ++i) {
                 const int4 cd = S.chunks[own_chunk(i)];
@@ -909,24 +889,23 @@ __global__ void __launch_bounds__(BLOCK, md_min_ctas(BLOCK, DENSE)) k_md_persist
                     if (S.dbg_fx && it == nsteps - 1) debug_force(S, set, slot, fx, fy);
                     kick_drift<T>(R, oi, vi, fx, fy, hk, dt, first, vscale, pout, vel, slot, vm, bad);
                 }
-                chunk_vmax<BLOCK>(S, vm, cd.x, s, s_vmax, vpar);
-                vpar ^= 1;
             }
         }
+        for (int o = 16; o > 0; o >>= 1) vm = fmaxf(vm, __shfl_xor_sync(0xffffffffu, vm, o));
+        if (lane == 0) s_vmax[tid >> 5] = vm;
         if (__syncthreads_or(bad) && tid == 0) atomicOr(&C->status, (int)DS_NONFINITE);
+        if (tid == 0) {
+            float m = 0.0f;
+            for (int w = 0; w < BLOCK / 32; ++w) m = fmaxf(m, s_vmax[w]);
+            atomicMax(&C->vmax[s % 3], __float_as_uint(m));   // non-negative floats order as uints
+        }
         // the barrier self-test: one CTA never arrives, so the others' wait
         // runs into its limit (nothing else is skipped; the CTA returns)
         if (it == 0 && S.dbg_leave_cta == (int)blockIdx.x) return;
         if (!grid_sync(bar, gen, S.timeout_ns)) return;
         cur ^= 1;
-        // every CTA accumulates the same bounds, in units of half the skin
-        int due_any = 0;
-        for (int r = tid; r < S.nrep; r += BLOCK) {
-            const unsigned v = *(volatile unsigned *)&S.vmax_rep[(long long)r * 3 + s % 3];
-            s_disp[r] += (double)__uint_as_float(v) * 1.0000001;
-            due_any |= s_disp[r] >= 1.0;
-        }
-        due_any = __syncthreads_or(due_any);
+        // every CTA accumulates the same bound, in units of half the skin
+        disp += (double)__uint_as_float(*(volatile unsigned *)&C->vmax[s % 3]) * 1.0000001;
         // ---- sampling pass
         const unsigned due = s_due;
         if (due) {
@@ -983,15 +962,15 @@ __global__ void __launch_bounds__(BLOCK, md_min_ctas(BLOCK, DENSE)) k_md_persist
                 flush_hist(S, sh_hist, hist_rep, due, s_win);
             }
         }
-        if (due_any) {
-            if (!rebuild<T, BLOCK>(S, set, cur, gen, nloc, s_desc, RB_DUE, s_disp)) return;
-            for (int r = tid; r < S.nrep; r += BLOCK)
-                if (s_disp[r] >= 1.0) s_disp[r] = 0.0;
+        if (disp >= 1.0) {
+            if (!rebuild<T, BLOCK>(S, set, cur, gen, nloc, s_desc, RB_ALL)) return;
+            disp = 0.0;
         }
-        __syncthreads();   // s_due / s_win / s_disp are rewritten in the next step
+        __syncthreads();   // s_due / s_win / s_vmax are rewritten in the next step
     }
     if (blockIdx.x == 0) {
-        for (int r = tid; r < S.nrep; r += BLOCK) S.disp_rep[r] = s_disp[r];
+        // every replica's bound is the batch's
+        for (int r = tid; r < S.nrep; r += BLOCK) S.disp_rep[r] = disp;
         if (tid == 0) {
             C->set = set;
             C->cur = cur;

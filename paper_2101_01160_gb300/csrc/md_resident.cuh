@@ -13,14 +13,17 @@
 // all replicas to the CTAs of one cooperative launch (one CTA per SM) by
 // list scheduling; each CTA runs its slabs one after another.
 //
-// Results equal k_md_persistent's bit for bit: the same per-replica rebuild
-// rule (canonical cells once the replica's displacement bound reaches half
-// the skin), the same canonicalisation and kick/drift arithmetic, and each
-// particle's force summed over the same pairs in the same order -- the 3x3
-// stencil of its cell row by row, column by column, by id inside a cell
-// (the lists are built in that order; pairs beyond rc add nothing, so when
-// a list was built does not matter).  Only the FP64 moment partial sums are
-// grouped per slab instead of per 32-slot group.
+// Every replica's trajectory equals, bit for bit, the one k_md_persistent
+// gives that replica alone: the rebuild rule is per replica (canonical cells
+// once the replica's displacement bound reaches half the skin -- the global
+// engine's rule for a single replica; for a batch it rebuilds all replicas
+// together), the canonicalisation and kick/drift arithmetic are the same,
+// and each particle's force is summed over the same pairs in the same order
+// -- the 3x3 stencil of its cell row by row, column by column, by id inside
+// a cell (the lists are built in that order; pairs beyond rc add nothing,
+// so when a list was built does not matter).  So a replica's results do not
+// depend on the batch, the slab plan or how md_step calls are split; only
+// the FP64 moment partial sums are grouped per slab.
 #pragma once
 
 #include "md_kernels.cuh"
@@ -137,17 +140,25 @@ __device__ __forceinline__ void res_fail(int *status, int flag) { atomicOr(statu
 // entry is the neighbour's index | (dcx + 1) << 14; a particle's entries are
 // in stencil order, rows dcy = -1, 0, 1 ending at lst + the two counts in
 // rend and at the next particle's start.
+// The dynamic shared memory of k_md_resident.  Slab arrays are addressed as
+// byte offsets into it, so that every access compiles to a shared-memory
+// load or store with 32-bit addresses.
+extern __shared__ __align__(16) unsigned char res_smem[];
+
 struct Slab {
-    float2 *off[2];   // [p_cap] own offsets (and build scratch in the spare one)
-    float2 *hoff;     // [2 h_cap] halo offsets
-    float2 *vel;      // [p_cap]
-    uint32_t *cell;   // [p_cap + 2 h_cap] packed cx | cy << 16
-    int32_t *id;      // [p_cap + 2 h_cap]
-    uint32_t *lst;    // [p_cap + 1] list starts
-    uint16_t *rend;   // [p_cap] entries of rows dcy = -1 and -1..0 (u8 each)
-    uint16_t *bidx;   // [2 h_cap] own slots of the first and the last row
-    uint16_t *ent;    // [e_cap]
+    uint32_t o_off[2], o_hoff, o_vel, o_cell, o_id, o_lst, o_rend, o_bidx, o_ent;
     int e_cap;
+    __device__ __forceinline__ float2 *off(int b) const { return reinterpret_cast<float2 *>(res_smem + o_off[b]); }
+    __device__ __forceinline__ float2 *hoff() const { return reinterpret_cast<float2 *>(res_smem + o_hoff); }
+    __device__ __forceinline__ float2 *vel() const { return reinterpret_cast<float2 *>(res_smem + o_vel); }
+    __device__ __forceinline__ uint32_t *cell() const { return reinterpret_cast<uint32_t *>(res_smem + o_cell); }
+    __device__ __forceinline__ int32_t *id() const { return reinterpret_cast<int32_t *>(res_smem + o_id); }
+    __device__ __forceinline__ uint32_t *lst() const { return reinterpret_cast<uint32_t *>(res_smem + o_lst); }
+    __device__ __forceinline__ uint16_t *rend() const { return reinterpret_cast<uint16_t *>(res_smem + o_rend); }
+    __device__ __forceinline__ uint16_t *bidx() const { return reinterpret_cast<uint16_t *>(res_smem + o_bidx); }
+    __device__ __forceinline__ uint16_t *ent() const { return reinterpret_cast<uint16_t *>(res_smem + o_ent); }
+    // build scratch in the spare own-offset buffer of cur
+    __device__ __forceinline__ unsigned char *scratch(int cur) const { return res_smem + o_off[cur ^ 1]; }
 };
 
 constexpr uint32_t RES_IDX = (1u << 14) - 1u;
@@ -169,21 +180,21 @@ __host__ __device__ inline size_t res_slab_bytes(int p_cap, int h_cap, int e_cap
            align16((size_t)e_cap * sizeof(uint16_t));
 }
 
-__device__ inline Slab res_layout(unsigned char *p, int p_cap, int h_cap, size_t avail) {
+__device__ inline Slab res_layout(uint32_t base, int p_cap, int h_cap, size_t avail) {
     Slab L;
     const size_t ph = (size_t)p_cap + 2 * (size_t)h_cap;
-    unsigned char *base = p;
-    const size_t ob = res_off_bytes(p_cap, h_cap);
-    L.off[0] = reinterpret_cast<float2 *>(p); p += ob;
-    L.off[1] = reinterpret_cast<float2 *>(p); p += ob;
-    L.hoff = reinterpret_cast<float2 *>(p); p += align16(2 * (size_t)h_cap * sizeof(float2));
-    L.vel = reinterpret_cast<float2 *>(p); p += align16((size_t)p_cap * sizeof(float2));
-    L.cell = reinterpret_cast<uint32_t *>(p); p += align16(ph * sizeof(uint32_t));
-    L.id = reinterpret_cast<int32_t *>(p); p += align16(ph * sizeof(int32_t));
-    L.lst = reinterpret_cast<uint32_t *>(p); p += align16(((size_t)p_cap + 1) * sizeof(uint32_t));
-    L.rend = reinterpret_cast<uint16_t *>(p); p += align16((size_t)p_cap * sizeof(uint16_t));
-    L.bidx = reinterpret_cast<uint16_t *>(p); p += align16(2 * (size_t)h_cap * sizeof(uint16_t));
-    L.ent = reinterpret_cast<uint16_t *>(p);
+    uint32_t p = base;
+    const uint32_t ob = (uint32_t)res_off_bytes(p_cap, h_cap);
+    L.o_off[0] = p; p += ob;
+    L.o_off[1] = p; p += ob;
+    L.o_hoff = p; p += (uint32_t)align16(2 * (size_t)h_cap * sizeof(float2));
+    L.o_vel = p; p += (uint32_t)align16((size_t)p_cap * sizeof(float2));
+    L.o_cell = p; p += (uint32_t)align16(ph * sizeof(uint32_t));
+    L.o_id = p; p += (uint32_t)align16(ph * sizeof(int32_t));
+    L.o_lst = p; p += (uint32_t)align16(((size_t)p_cap + 1) * sizeof(uint32_t));
+    L.o_rend = p; p += (uint32_t)align16((size_t)p_cap * sizeof(uint16_t));
+    L.o_bidx = p; p += (uint32_t)align16(2 * (size_t)h_cap * sizeof(uint16_t));
+    L.o_ent = p;
     const size_t used = (size_t)(p - base);
     L.e_cap = used < avail ? (int)((avail - used) / sizeof(uint16_t)) : 0;
     return L;
@@ -192,7 +203,7 @@ __device__ inline Slab res_layout(unsigned char *p, int p_cap, int h_cap, size_t
 // Offset of own or halo particle j in the buffer holding the current
 // positions.
 __device__ __forceinline__ float2 res_off(const Slab &L, int cur, int p_cap, int j) {
-    return j < p_cap ? L.off[cur][j] : L.hoff[j - p_cap];
+    return j < p_cap ? L.off(cur)[j] : L.hoff()[j - p_cap];
 }
 
 // State of the slab a CTA is running.
@@ -238,10 +249,10 @@ __device__ bool res_load(const SysDev &S, const RepDev &R, const Slab &L, SlabRu
         const int at = p + block_excl_scan(f, s_w, &tot);
         if (f) {
             if (at < X.J.p_cap) {
-                L.off[X.cur][at] = pos[slot];
-                L.vel[at] = vel[slot];
-                L.cell[at] = c;
-                L.id[at] = pid[slot];
+                L.off(X.cur)[at] = pos[slot];
+                L.vel()[at] = vel[slot];
+                L.cell()[at] = c;
+                L.id()[at] = pid[slot];
             } else {
                 over = true;
             }
@@ -271,10 +282,10 @@ __device__ bool res_store(const SysDev &S, const ResDev &D, const RepDev &R, con
     float2 *vel = static_cast<float2 *>(S.vel[nset]);
     const int b = R.pbase + s_off;
     for (int i = threadIdx.x; i < X.p; i += RES_THREADS) {
-        pos[b + i] = L.off[X.cur][i];
-        vel[b + i] = L.vel[i];
-        S.cell[nset][b + i] = L.cell[i];
-        S.pid[nset][b + i] = L.id[i];
+        pos[b + i] = L.off(X.cur)[i];
+        vel[b + i] = L.vel()[i];
+        S.cell[nset][b + i] = L.cell()[i];
+        S.pid[nset][b + i] = L.id()[i];
     }
     // the next job may reuse slab_n only after every gang member read it
     return gang_sync(bar, X.J.g, my_gen, &S.ctl->status, S.timeout_ns);
@@ -297,15 +308,15 @@ __device__ bool res_halo_full(const SysDev &S, const ResDev &D, const RepDev &R,
         int n = 0;
         for (int base = 0; base < X.p; base += RES_THREADS) {
             const int i = base + (int)threadIdx.x;
-            const int f = i < X.p && (int)(L.cell[i] >> 16) == rows[side];
+            const int f = i < X.p && (int)(L.cell()[i] >> 16) == rows[side];
             int tot;
             const int at = n + block_excl_scan(f, s_w, &tot);
             if (f) {
                 if (at < X.J.h_cap) {
-                    L.bidx[side * X.J.h_cap + at] = (uint16_t)i;
+                    L.bidx()[side * X.J.h_cap + at] = (uint16_t)i;
                     const long long gi = ((long long)me * 2 + side) * D.hmax + at;
-                    D.halo_ci[gi] = make_uint2(L.cell[i], (uint32_t)L.id[i]);
-                    D.halo_off[(((long long)me * 2 + side) * 2 + X.par) * D.hmax + at] = L.off[X.cur][i];
+                    D.halo_ci[gi] = make_uint2(L.cell()[i], (uint32_t)L.id()[i]);
+                    D.halo_off[(((long long)me * 2 + side) * 2 + X.par) * D.hmax + at] = L.off(X.cur)[i];
                 } else {
                     over = true;
                 }
@@ -330,9 +341,9 @@ __device__ bool res_halo_full(const SysDev &S, const ResDev &D, const RepDev &R,
         const int o = X.J.p_cap + h * X.J.h_cap;
         for (int i = threadIdx.x; i < n; i += RES_THREADS) {
             const uint2 ci = D.halo_ci[((long long)src[h] * 2 + side) * D.hmax + i];
-            L.cell[o + i] = ci.x;
-            L.id[o + i] = (int32_t)ci.y;
-            L.hoff[h * X.J.h_cap + i] = D.halo_off[(((long long)src[h] * 2 + side) * 2 + X.par) * D.hmax + i];
+            L.cell()[o + i] = ci.x;
+            L.id()[o + i] = (int32_t)ci.y;
+            L.hoff()[h * X.J.h_cap + i] = D.halo_off[(((long long)src[h] * 2 + side) * 2 + X.par) * D.hmax + i];
         }
     }
     __syncthreads();
@@ -355,7 +366,7 @@ __device__ bool res_lists(const SysDev &S, const RepDev &R, const Slab &L, const
     const int ncells = G * ncol;
     const int pc = X.J.p_cap;
     const int ph = pc + 2 * X.J.h_cap;
-    unsigned char *scr = reinterpret_cast<unsigned char *>(L.off[X.cur ^ 1]);
+    unsigned char *scr = L.scratch(X.cur);
     uint16_t *mem = reinterpret_cast<uint16_t *>(scr);
     int32_t *ccs = reinterpret_cast<int32_t *>(scr + align16((size_t)ph * sizeof(uint16_t)));
     auto member = [&](int j) {   // own or filled halo slot
@@ -372,7 +383,7 @@ __device__ bool res_lists(const SysDev &S, const RepDev &R, const Slab &L, const
     for (int c = threadIdx.x; c <= ncells; c += RES_THREADS) ccs[c] = 0;
     __syncthreads();
     for (int j = threadIdx.x; j < ph; j += RES_THREADS) {
-        const int c = member(j) ? ccell(L.cell[j]) : -1;
+        const int c = member(j) ? ccell(L.cell()[j]) : -1;
         if (c >= 0) atomicAdd(&ccs[c], 1);
     }
     __syncthreads();
@@ -390,7 +401,7 @@ __device__ bool res_lists(const SysDev &S, const RepDev &R, const Slab &L, const
     }
     __syncthreads();
     for (int j = threadIdx.x; j < ph; j += RES_THREADS) {
-        const int c = member(j) ? ccell(L.cell[j]) : -1;
+        const int c = member(j) ? ccell(L.cell()[j]) : -1;
         if (c >= 0) mem[atomicSub(&ccs[c], 1) - 1] = (uint16_t)j;
     }
     __syncthreads();
@@ -399,13 +410,13 @@ __device__ bool res_lists(const SysDev &S, const RepDev &R, const Slab &L, const
         const int a = ccs[c], b = ccs[c + 1];
         for (int m = a + 1; m < b; ++m) {
             const uint16_t v = mem[m];
-            const uint32_t kx = L.cell[v] & 0xffffu;
-            const int ki = L.id[v];
+            const uint32_t kx = L.cell()[v] & 0xffffu;
+            const int ki = L.id()[v];
             int q = m - 1;
             while (q >= a) {
                 const uint16_t u = mem[q];
-                const uint32_t ux = L.cell[u] & 0xffffu;
-                if (ux < kx || (ux == kx && L.id[u] < ki)) break;
+                const uint32_t ux = L.cell()[u] & 0xffffu;
+                if (ux < kx || (ux == kx && L.id()[u] < ki)) break;
                 mem[q + 1] = u;
                 --q;
             }
@@ -414,7 +425,7 @@ __device__ bool res_lists(const SysDev &S, const RepDev &R, const Slab &L, const
     }
     __syncthreads();
     const float h = R.hf, rv2 = R.rv2f;
-    const float2 *off = L.off[X.cur];
+    const float2 *off = L.off(X.cur);
     // pass 1 counts (per stencil row), pass 2 writes
     bool over = false;
     int e0 = 0;
@@ -423,11 +434,11 @@ __device__ bool res_lists(const SysDev &S, const RepDev &R, const Slab &L, const
             const int i = base + (int)threadIdx.x;
             int cnt = 0;
             if (i < X.p) {
-                const uint32_t ci = L.cell[i];
+                const uint32_t ci = L.cell()[i];
                 const int cx = (int)(ci & 0xffffu), cy = (int)(ci >> 16);
                 const float2 oi = off[i];
                 uint32_t rows = 0;
-                uint32_t e = pass ? L.lst[i] : 0u;
+                uint32_t e = pass ? L.lst()[i] : 0u;
                 for (int oy = -1; oy <= 1; ++oy) {
                     const int ty = wrap1(cy + oy, nc);
                     const int grow = X.J.g == 1 ? ty : res_relrow(X, nc, cy) + oy;
@@ -439,14 +450,14 @@ __device__ bool res_lists(const SysDev &S, const RepDev &R, const Slab &L, const
                         const uint32_t tcell = (uint32_t)tx | ((uint32_t)ty << 16);
                         for (int m = ccs[cc]; m < ccs[cc + 1]; ++m) {
                             const int j = mem[m];
-                            const uint32_t cj = L.cell[j];
+                            const uint32_t cj = L.cell()[j];
                             if ((cj & 0xffffu) > (uint32_t)tx) break;
                             if (cj != tcell || j == i) continue;
                             const float2 o = res_off(L, X.cur, pc, j);
                             const float rx = o.x + sx, ry = o.y + sy;
                             if (rx * rx + ry * ry < rv2) {
                                 if (pass && (int)e < L.e_cap)
-                                    L.ent[e] = (uint16_t)((uint32_t)j | ((uint32_t)(ox + 1) << 14));
+                                    L.ent()[e] = (uint16_t)((uint32_t)j | ((uint32_t)(ox + 1) << 14));
                                 ++e;
                                 ++cnt;
                             }
@@ -455,19 +466,19 @@ __device__ bool res_lists(const SysDev &S, const RepDev &R, const Slab &L, const
                     if (oy < 1) rows |= (uint32_t)min(cnt, 255) << (8 * (oy + 1));
                 }
                 if (!pass) {
-                    L.rend[i] = (uint16_t)rows;
+                    L.rend()[i] = (uint16_t)rows;
                     over |= cnt > RES_MAXLIST;
                 }
             }
             if (!pass) {
                 int tot;
                 const int at = e0 + block_excl_scan(cnt, s_w, &tot);
-                if (i < X.p) L.lst[i] = (uint32_t)at;
+                if (i < X.p) L.lst()[i] = (uint32_t)at;
                 e0 += tot;
             }
         }
         if (!pass) {
-            if (threadIdx.x == 0) L.lst[X.p] = (uint32_t)e0;
+            if (threadIdx.x == 0) L.lst()[X.p] = (uint32_t)e0;
             over |= e0 > L.e_cap;
             if (__syncthreads_or(over)) {
                 res_fail(&S.ctl->status, DS_CAPACITY);
@@ -486,10 +497,10 @@ __device__ bool res_lists(const SysDev &S, const RepDev &R, const Slab &L, const
 __device__ bool res_canon_migrate(const SysDev &S, const ResDev &D, const RepDev &R, const Slab &L,
                                   SlabRun &X, unsigned &my_gen, unsigned *bar, int *s_w) {
     const float h = R.hf;
-    float2 *off = L.off[X.cur];
+    float2 *off = L.off(X.cur);
     for (int i = threadIdx.x; i < X.p; i += RES_THREADS) {
         float2 o = off[i];
-        const uint32_t cpk = L.cell[i];
+        const uint32_t cpk = L.cell()[i];
         const int sx = o.x >= h ? 1 : (o.x < 0.0f ? -1 : 0);
         const int sy = o.y >= h ? 1 : (o.y < 0.0f ? -1 : 0);
         o.x -= (float)sx * h;
@@ -497,7 +508,7 @@ __device__ bool res_canon_migrate(const SysDev &S, const ResDev &D, const RepDev
         const int ncx = wrap1((int)(cpk & 0xffffu) + sx, R.nc);
         const int ncy = wrap1((int)(cpk >> 16) + sy, R.nc);
         off[i] = o;
-        L.cell[i] = (uint32_t)ncx | ((uint32_t)ncy << 16);
+        L.cell()[i] = (uint32_t)ncx | ((uint32_t)ncy << 16);
     }
     __syncthreads();
     if (X.J.g == 1) return true;
@@ -515,9 +526,9 @@ __device__ bool res_canon_migrate(const SysDev &S, const ResDev &D, const RepDev
         int id = 0, dir = -1;
         if (i < X.p) {
             o = off[i];
-            v = L.vel[i];
-            c = L.cell[i];
-            id = L.id[i];
+            v = L.vel()[i];
+            c = L.cell()[i];
+            id = L.id()[i];
             const int cy = (int)(c >> 16);
             if (!(cy >= X.J.r0 && cy < X.J.r1)) dir = cy == top ? 0 : 1;
         }
@@ -528,9 +539,9 @@ __device__ bool res_canon_migrate(const SysDev &S, const ResDev &D, const RepDev
         if (i < X.p) {
             if (dir < 0) {
                 off[ak] = o;
-                L.vel[ak] = v;
-                L.cell[ak] = c;
-                L.id[ak] = id;
+                L.vel()[ak] = v;
+                L.cell()[ak] = c;
+                L.id()[ak] = id;
             } else {
                 const int at = dir == 0 ? a0 : a1;
                 if (at < D.hmax) {
@@ -568,9 +579,9 @@ __device__ bool res_canon_migrate(const SysDev &S, const ResDev &D, const RepDev
             const float4 a = D.mig_a[gi];
             const uint2 b = D.mig_b[gi];
             off[p + t] = make_float2(a.x, a.y);
-            L.vel[p + t] = make_float2(a.z, a.w);
-            L.cell[p + t] = b.x;
-            L.id[p + t] = (int32_t)b.y;
+            L.vel()[p + t] = make_float2(a.z, a.w);
+            L.cell()[p + t] = b.x;
+            L.id()[p + t] = (int32_t)b.y;
         }
         p += n;
     }
@@ -583,17 +594,18 @@ __device__ bool res_canon_migrate(const SysDev &S, const ResDev &D, const RepDev
 // Force on own particle i from its list (row by row, the column of each
 // entry from its tag: the arithmetic of lj_list), then the velocity-Verlet
 // update of kick_drift into the other own-offset buffer.
-__device__ __forceinline__ void res_force_kick(const SysDev &S, const RepDev &R, const Slab &L, const SlabRun &X,
-                                               int i, bool first, bool dbg, float &vm, bool &bad) {
-    const float2 *off = L.off[X.cur];
+__device__ __forceinline__ void res_force_kick(const SysDev &S, const RepDev &R, const float *P, const Slab &L,
+                                               const SlabRun &X, int i, bool first, bool dbg, float &vm, bool &bad) {
+    const float2 *off = L.off(X.cur);
+    const float2 *hoff = L.hoff();
+    const uint16_t *ent = L.ent();
     const int pc = X.J.p_cap;
     const float2 oi = off[i];
-    const float h = R.hf;
-    const float rc2 = R.rc2f, eps24 = 24.0f * R.epsf, sig2 = R.sig2f;
+    const float h = P[0], rc2 = P[1], eps24 = P[2], sig2 = P[3];
     const float sx0 = -h - oi.x, sx1 = -oi.x, sx2 = h - oi.x;
     const float sys[3] = {-h - oi.y, -oi.y, h - oi.y};
-    const uint32_t st = L.lst[i], en = L.lst[i + 1];
-    const uint32_t re = L.rend[i];
+    const uint32_t st = L.lst()[i], en = L.lst()[i + 1];
+    const uint32_t re = L.rend()[i];
     const uint32_t ends[3] = {st + (re & 0xffu), st + (re >> 8), en};
     float fx = 0.0f, fy = 0.0f;
     double pe_unused = 0.0, fa_unused = 0.0;
@@ -602,20 +614,19 @@ __device__ __forceinline__ void res_force_kick(const SysDev &S, const RepDev &R,
     for (int row = 0; row < 3; ++row) {
         const float sy = sys[row];
         for (; e < ends[row]; ++e) {
-            const uint32_t v = L.ent[e];
+            const uint32_t v = ent[e];
             const int j = (int)(v & RES_IDX);
             const uint32_t t = v >> 14;
-            const float2 o = j < pc ? off[j] : L.hoff[j - pc];
+            const float2 o = j < pc ? off[j] : hoff[j - pc];
             const float sx = t == 0 ? sx0 : (t == 1 ? sx1 : sx2);
             lj_pair_acc<float, false>(o.x + sx, o.y + sy, rc2, eps24, sig2, fx, fy, 0.0, pe_unused, fa_unused);
         }
     }
     if (dbg) {
-        S.dbg_fx[L.id[i]] = (double)fx;
-        S.dbg_fy[L.id[i]] = (double)fy;
+        S.dbg_fx[L.id()[i]] = (double)fx;
+        S.dbg_fy[L.id()[i]] = (double)fy;
     }
-    const float vscale = (float)(R.dt / R.half_skin);
-    kick_drift<float>(R, oi, L.vel[i], fx, fy, R.hkf, R.dtf, first, vscale, L.off[X.cur ^ 1], L.vel, i, vm, bad);
+    kick_drift<float>(R, oi, L.vel()[i], fx, fy, P[4], P[5], first, P[6], L.off(X.cur ^ 1), L.vel(), i, vm, bad);
 }
 
 // Block maximum of v over the CTA into thread 0 (fixed order).
@@ -634,7 +645,6 @@ __device__ __forceinline__ float block_max(float v, float *s_f) {
 // Runs every slab job of this CTA for nsteps steps from step0.
 __global__ void __launch_bounds__(RES_THREADS, 1) k_md_resident(SysDev S, ResDev D, long long step0,
                                                                 long long nsteps, int phase_half) {
-    extern __shared__ __align__(16) unsigned char smem[];
     __shared__ int s_w[33];
     __shared__ float s_f[32];
     __shared__ double s_dm[2][32];
@@ -642,18 +652,19 @@ __global__ void __launch_bounds__(RES_THREADS, 1) k_md_resident(SysDev S, ResDev
     __shared__ long long s_win[MD_MAX_LG];
     __shared__ double s_disp;
     __shared__ int s_rebuild;
+    __shared__ float s_par[8];   // the replica's FP32 constants: h, rc^2, 24 eps, sigma^2, dt/2m, dt, dt/(skin/2)
     Control *C = S.ctl;
     const int tid = threadIdx.x, lane = tid & 31;
     const int set = C->set, gcur = C->cur;
     const int per_lg = S.n_dx * S.nb;
-    int *sh_hist = reinterpret_cast<int *>(smem);
-    unsigned char *slab_mem = smem + smem_hist_bytes(S.n_lg, S.n_dx, S.nb);
-    const size_t avail = (size_t)D.smem_bytes - smem_hist_bytes(S.n_lg, S.n_dx, S.nb);
+    int *sh_hist = reinterpret_cast<int *>(res_smem);
+    const uint32_t slab_base = (uint32_t)smem_hist_bytes(S.n_lg, S.n_dx, S.nb);
+    const size_t avail = (size_t)D.smem_bytes - slab_base;
     for (int jb = D.job_start[blockIdx.x]; jb < D.job_start[blockIdx.x + 1]; ++jb) {
         SlabRun X;
         X.J = D.jobs[jb];
         const RepDev &R = S.reps[X.J.rep];
-        const Slab L = res_layout(slab_mem, X.J.p_cap, X.J.h_cap, avail);
+        const Slab L = res_layout(slab_base, X.J.p_cap, X.J.h_cap, avail);
         X.up = X.J.cta0 + (X.J.k + 1) % X.J.g;
         X.down = X.J.cta0 + (X.J.k + X.J.g - 1) % X.J.g;
         X.cur = 0;
@@ -662,7 +673,18 @@ __global__ void __launch_bounds__(RES_THREADS, 1) k_md_resident(SysDev S, ResDev
         unsigned my_gen = 0;
         if (tid == 0) {
             my_gen = ld_acquire_gpu(&bar[1]);
+            // the step's maximum starts from zero (a global-engine launch in
+            // between leaves these slots untouched); before the first
+            // barrier, so before any gang member adds to it
+            if (X.J.k == 0) S.vmax_rep[(long long)X.J.rep * 3 + step0 % 3] = 0u;
             s_disp = S.disp_rep[X.J.rep];
+            s_par[0] = R.hf;
+            s_par[1] = R.rc2f;
+            s_par[2] = 24.0f * R.epsf;   // the eps24 of lj_list
+            s_par[3] = R.sig2f;
+            s_par[4] = R.hkf;
+            s_par[5] = R.dtf;
+            s_par[6] = (float)(R.dt / R.half_skin);
         }
         for (int e = tid; e < S.n_lg * per_lg; e += RES_THREADS) sh_hist[e] = 0;
         if (!res_load(S, R, L, X, set, gcur, s_w)) {
@@ -692,7 +714,7 @@ __global__ void __launch_bounds__(RES_THREADS, 1) k_md_resident(SysDev S, ResDev
             const bool dbg = S.dbg_fx && it == nsteps - 1;
             float vm = 0.0f;
             bool bad = false;
-            for (int i = tid; i < X.p; i += RES_THREADS) res_force_kick(S, R, L, X, i, first, dbg, vm, bad);
+            for (int i = tid; i < X.p; i += RES_THREADS) res_force_kick(S, R, s_par, L, X, i, first, dbg, vm, bad);
             if (__syncthreads_or(bad) && tid == 0) atomicOr(&C->status, (int)DS_NONFINITE);
             const float m = block_max(vm, s_f);
             if (tid == 0) atomicMax(&S.vmax_rep[(long long)X.J.rep * 3 + s % 3], __float_as_uint(m));
@@ -702,7 +724,7 @@ __global__ void __launch_bounds__(RES_THREADS, 1) k_md_resident(SysDev S, ResDev
                 for (int side = 0; side < 2; ++side)
                     for (int t = tid; t < X.nb[side]; t += RES_THREADS)
                         D.halo_off[(((long long)blockIdx.x * 2 + side) * 2 + npar) * D.hmax + t] =
-                            L.off[nx][L.bidx[side * X.J.h_cap + t]];
+                            L.off(nx)[L.bidx()[side * X.J.h_cap + t]];
             if (!gang_sync(bar, X.J.g, my_gen, &C->status, S.timeout_ns)) return;
             if (tid == 0) {
                 const unsigned v = *(volatile unsigned *)&S.vmax_rep[(long long)X.J.rep * 3 + s % 3];
@@ -713,7 +735,7 @@ __global__ void __launch_bounds__(RES_THREADS, 1) k_md_resident(SysDev S, ResDev
                 const int src[2] = {X.up, X.down};
                 for (int hh = 0; hh < 2; ++hh)
                     for (int t = tid; t < X.nh[hh]; t += RES_THREADS)
-                        L.hoff[hh * X.J.h_cap + t] =
+                        L.hoff()[hh * X.J.h_cap + t] =
                             D.halo_off[(((long long)src[hh] * 2 + hh) * 2 + npar) * D.hmax + t];
             }
             X.cur = nx;
@@ -730,9 +752,9 @@ __global__ void __launch_bounds__(RES_THREADS, 1) k_md_resident(SysDev S, ResDev
                     uint32_t cpk = 0;
                     float2 on{};
                     if (active) {
-                        id = L.id[i];
-                        cpk = L.cell[i];
-                        on = L.off[X.cur][i];
+                        id = L.id()[i];
+                        cpk = L.cell()[i];
+                        on = L.off(X.cur)[i];
                     }
                     for (int k = 0; k < S.n_lg; ++k) {
                         if (!(due >> k & 1u)) continue;

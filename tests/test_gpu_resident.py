@@ -1,14 +1,16 @@
 """The shared-memory-resident engine (md_tune staging 4) against the global
 engine and the oracle, through the C-ABI.
 
-Both engines apply the same per-replica rebuild rule and sum every force
-over the same pairs in the same order, so their trajectories, snapshots
-and integer histograms must be identical bit for bit, whatever the slab
-plan, the launch splitting of md_step and the launch shape of the global
-engine.  Only the FP64 moment sums are grouped differently: they must agree
-to 1e-12 relative.  The global engine itself is checked against the oracle
-elsewhere (forces, binning, trajectories); the list forces of the resident
-engine are also checked against the oracle directly here.
+The resident engine keeps one rebuild bound per replica; the global engine
+keeps one for its whole batch, which for a batch of one replica is the same
+rule.  Both sum every force over the same pairs in the same order with the
+same arithmetic, so each replica of a resident batch must follow, bit for
+bit, the trajectory the global engine gives that replica alone (positions,
+velocities, snapshots, integer histograms), whatever the slab plan and the
+splitting of md_step calls.  Only the FP64 moment sums are grouped
+differently: they must agree to 1e-12 relative.  The global engine itself
+is checked against the oracle elsewhere; the resident engine's own list
+forces are also checked against the oracle here.
 """
 
 import numpy as np
@@ -42,11 +44,25 @@ def _run(mdlg, params, cat, engine, chunks):
         s.tune(256, 1, 3)
     for c in chunks:
         s.step(c)
+    R = len(params)
     out = {"state": s.get_state(), "snap": [[t.cpu().numpy() for t in s.get_snapshot(k)] for k in range(2)]}
-    out["hist"] = [[[s.hist_raw(r, k, d) for d in range(2)] for k in range(2)] for r in range(len(params))]
-    out["mom"] = [[_bars.moment_sums(s, r, k, params[r].n) for k in range(2)] for r in range(len(params))]
+    out["hist"] = [[[s.hist_raw(r, k, d) for d in range(2)] for k in range(2)] for r in range(R)]
+    out["mom"] = [[_bars.moment_sums(s, r, k, params[r].n) for k in range(2)] for r in range(R)]
     s.close()
     return out
+
+
+def _alone(mdlg, params, cat, chunks):
+    """Each replica run alone on the global engine, results concatenated in
+    replica order."""
+    base = np.concatenate([[0], np.cumsum([p.n for p in params])])
+    outs = []
+    for r, p in enumerate(params):
+        sl = slice(base[r], base[r + 1])
+        outs.append(_run(mdlg, [p], [a[sl] for a in cat], "global", chunks))
+    return {"state": [np.concatenate([o["state"][q] for o in outs]) for q in range(4)],
+            "snap": [[np.concatenate([o["snap"][k][q] for o in outs]) for q in range(3)] for k in range(2)],
+            "hist": [o["hist"][0] for o in outs], "mom": [o["mom"][0] for o in outs]}
 
 
 def _same(a, b):
@@ -67,22 +83,23 @@ def _same(a, b):
 @pytest.mark.parametrize("spec", [
     [(5000, 0.2, 5.0)],                        # one slab
     [(60000, 0.25, 8.0)],                      # one replica over many slabs
-    [(4096, 0.02, 20.0), (30000, 0.3, 1.0), (9000, 0.1, 12.0)],
 ])
-def test_resident_equals_global_engine(mdlg, spec):
+def test_resident_equals_global_engine_single_replica(mdlg, spec):
     params, cat = _batch(mdlg, spec, seed0=70)
     a = _run(mdlg, params, cat, "global", (800,))
     b = _run(mdlg, params, cat, "resident", (300, 1, 499))
     _same(a, b)
 
 
-def test_resident_uneven_batch_equals_global_engine(mdlg):
-    """16 replicas of the bench's draw recipe (about 360k particles)."""
-    Ns, phis, Ts = inputs.ensemble_params(16, seed=11)
+@pytest.mark.parametrize("R,seed", [(3, 21), (16, 11)])
+def test_resident_batch_equals_replicas_alone(mdlg, R, seed):
+    """R replicas of the bench's draw recipe (16: about 360k particles) on
+    the resident engine against each replica alone on the global engine."""
+    Ns, phis, Ts = inputs.ensemble_params(R, seed=seed)
     spec = [(int(n), float(p), float(t)) for n, p, t in zip(Ns, phis, Ts)]
     params, cat = _batch(mdlg, spec, seed0=900)
-    a = _run(mdlg, params, cat, "global", (1000,))
-    b = _run(mdlg, params, cat, "resident", (1000,))
+    a = _alone(mdlg, params, cat, (1000,))
+    b = _run(mdlg, params, cat, "resident", (600, 400))
     _same(a, b)
 
 
