@@ -17,7 +17,8 @@ phi = 0.0784, T = 20, FP32, five sampling intervals x three lattices) and
 the same system in plain FP64.
 
 Output: one JSON line (rank 0).  --impl reference times the FP64 CPU oracle
-on a bounded sample of the same workload.
+on all host threads on a bounded sample of the same workload (16 of the 256
+replicas, one 400-step window per step).
 """
 
 from __future__ import annotations
@@ -64,18 +65,50 @@ def _peaks(key="hbm_gbs", fallback=6800.0):
         return fallback, "fallback"
 
 
-def _profile_traffic():
-    """DRAM bytes per bench-step launch of the persistent kernel, from the
-    committed ncu summary (None when absent or stale)."""
-    p = os.path.join(ROOT, "profiles", "k_md_persistent_batched256.md")
+# DRAM traffic of one bench-step launch of the global engine's kernel on this
+# workload: dram__bytes_read.sum + dram__bytes_write.sum from one ncu capture
+# of k_md_persistent<float,256,1> (the launch shape the autotuner picks),
+# copied here with its provenance; it is reported only for that kernel and
+# launch shape, and must be re-measured when the kernel changes.
+MD_TRAFFIC = {"kernel": "k_md_persistent<float,256,1>", "bytes_per_launch": None,
+              "source": "ncu --metrics dram__bytes_read.sum,dram__bytes_write.sum, 400-step launch "
+                        "of the 256-replica ensemble (profiles/k_md_persistent_batched256.md)"}
+
+
+def _cpu_model():
+    """CPU model of this host as the OS reports it (lscpu, else /proc/cpuinfo)."""
     try:
-        for line in open(p):
-            if line.startswith("traffic_bytes_per_launch:"):
-                v = line.split(":", 1)[1].strip()
-                return None if v in ("", "null") else float(v)
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for ln in out.splitlines():
+            if ln.strip().lower().startswith("model name"):
+                return ln.split(":", 1)[1].strip()
+    except (OSError, subprocess.SubprocessError):
+        pass
+    try:
+        for ln in open("/proc/cpuinfo"):
+            if ln.lower().startswith(("model name", "cpu part", "hardware")):
+                return ln.split(":", 1)[1].strip()
     except OSError:
         pass
-    return None
+    return "unknown"
+
+
+def _flops_per_particle_step(ens, skin=SKIN, rc=2.5):
+    """Algorithmic flops of one particle-step of the list-based LJ step
+    (full neighbour lists, each pair evaluated from both sides), averaged
+    over the particles of the ensemble: per listed pair the pair vector and
+    r^2 (5 flops), per pair within rc the force (13 more: 1/r^2, s^6, the
+    force factor and two multiply-adds), per particle the two half kicks,
+    the drift and the speed bound (16).  Mean counts from the density:
+    pi rc^2 n pairs within rc, pi (rc + skin)^2 n listed."""
+    tot, num = 0.0, 0.0
+    for (n, L, *_rest) in ens:
+        dens = n / (L * L)
+        within = np.pi * rc * rc * dens
+        listed = np.pi * (rc + skin) ** 2 * dens
+        num += n * (5.0 * listed + 13.0 * within + 16.0)
+        tot += n
+    return num / tot
 
 
 class ClockSampler:
@@ -379,6 +412,7 @@ def run_ours(args):
     feq_dev = torch.empty((N_REP, 3 * nb + mdlg.FEQB_STATS), dtype=torch.float64, device="cuda")
     flush = torch.empty(2 * L2_BYTES, dtype=torch.uint8, device="cuda")
     shape = sysm.autotune(100)      # launch shape (untimed set-up; real MD steps)
+    peaks = measured_alu_peaks(mdlg)
 
     for _ in range(args.warmup):
         sysm.step(MD_PER_STEP)
@@ -405,11 +439,21 @@ def run_ours(args):
     ms_per_step = t_max / args.steps
     value = ps_all / (t_max * 1e-3)
     stats = feq_dev[:, 3 * nb:].cpu().numpy()
-    feq_err = {"max_abs_md_vs_wsg": float(stats[:, 6].max()),
-               "max_abs_md_vs_gauss": float(stats[:, 4].max()),
+    fd = feq_dev.cpu().numpy()
+    dw = np.abs(fd[:, :nb] - fd[:, 2 * nb:3 * nb])
+    r_w, i_w = np.unravel_index(int(np.argmax(dw)), dw.shape)
+    dg = np.abs(fd[:, :nb] - fd[:, nb:2 * nb])
+    r_g, i_g = np.unravel_index(int(np.argmax(dg)), dg.shape)
+    # 3 sigma of the measured value there: batch means over blocks of windows
+    _, se_w, _ = sysm.feq_measured(int(r_w), 0, 0, symmetrize=True)
+    _, se_g, _ = sysm.feq_measured(int(r_g), 0, 0, symmetrize=True)
+    feq_err = {"max_abs_md_vs_wsg": float(dw[r_w, i_w]), "max_abs_md_vs_wsg_3sigma": float(3 * se_w[i_w]),
+               "max_abs_md_vs_gauss": float(dg[r_g, i_g]), "max_abs_md_vs_gauss_3sigma": float(3 * se_g[i_g]),
+               "at": {"wsg": [int(r_w), int(i_w)], "gauss": [int(r_g), int(i_g)]},
                "median_kl_md_wsg": float(np.median(stats[:, 7])),
                "median_kl_md_gauss": float(np.median(stats[:, 5])),
-               "windows": int(stats[0, 8])}
+               "windows": int(stats[0, 8]),
+               "sigma": "batch means over 32 blocks of windows, symmetric-set averages"}
 
     # end to end through the C-ABI with host buffers: upload the (equilibrated)
     # state from pinned host memory, run one window, read the f_eq stage back
@@ -431,6 +475,7 @@ def run_ours(args):
     info = sysm.info()
     sysm.close()
 
+    peak, peak_kind = _peaks()
     variants = {}
     if not args.no_variants and rank == 0:
         L1 = inputs.box_length(N1, PHI1)
@@ -442,14 +487,31 @@ def run_ours(args):
             variants[name] = _time_variant(mdlg, torch, p, st1, 2000)
             variants[name]["workload"] = ("N=262144 phi=0.0784 T=20, dt_lg {0.05..1.0} x dx "
                                           "{0.5,1,2}, one 2000-step launch")
-        variants["batched_fp32_over_plain_fp64"] = (value / ws) / variants["plain_fp64"]["value"]
+        v64 = variants["plain_fp64"]
+        f64 = _flops_per_particle_step([(N1, L1)], skin=0.5)
+        ach = f64 * v64["value"] / 1e12
+        hbm_ps = peak * 1e9 / 64.0                      # 32 B read + 32 B written per particle-step
+        alu_ps = peaks["fp64_tflops"] * 1e12 / f64
+        v64["roofline"] = {"bound": "fp64_alu" if alu_ps < hbm_ps else "hbm", "achieved": ach,
+                           "peak": peaks["fp64_tflops"], "unit": "TFLOP/s", "frac": ach / peaks["fp64_tflops"],
+                           "flops_per_particle_step": f64, "hbm_frac": 64.0 * v64["value"] / (peak * 1e9),
+                           "bound_particle_steps_per_s": min(hbm_ps, alu_ps),
+                           "frac_of_bound": v64["value"] / min(hbm_ps, alu_ps)}
+        variants["equal_accuracy"] = _equal_accuracy(mdlg, torch)
         variants["surrogate_inference"] = _time_surrogate(mdlg, torch)
         variants["disp_hist"] = _time_disp_hist(mdlg, torch)
         variants["local_fields"] = _time_local_fields(mdlg, torch)
 
-    peak, peak_kind = _peaks()
     kern_avg_s = (sum(kern_ms) / len(kern_ms)) * 1e-3
     achieved = BYTES_PER_PARTICLE_STEP * ntot * MD_PER_STEP / kern_avg_s / 1e9
+    kname = ("k_md_resident" if shape[2] == 4 else
+             f"k_md_persistent<float,{shape[0]},{int(shape[2] == 3)}>")
+    traffic = MD_TRAFFIC["bytes_per_launch"] if kname == MD_TRAFFIC["kernel"] else None
+    fpps = _flops_per_particle_step(ens)
+    alu = {"bound": "alu", "achieved": fpps * ntot * MD_PER_STEP / kern_avg_s / 1e12,
+           "peak": peaks["fp32_tflops"], "unit": "TFLOP/s",
+           "flops_per_particle_step": fpps, "peak_kind": "measured FP32 FMA throughput (this run)"}
+    alu["frac"] = alu["achieved"] / alu["peak"]
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
@@ -459,13 +521,16 @@ def run_ours(args):
                    "l2": "flushed between timed steps (256 MB write)",
                    "launch_shape": {"block_threads": shape[0], "per_thread": shape[1],
                                     "staging": {1: "shared", 2: "global",
-                                                3: "global, full-occupancy registers"}[shape[2]]},
+                                                3: "global, full-occupancy registers",
+                                                4: "shared-memory-resident slabs"}[shape[2]]},
                    "parallelism": f"replicas x{ws}"},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                     "frac": achieved / peak, "traffic": _profile_traffic(),
-                     "kernel": f"k_md_persistent<float,{shape[0]},{int(shape[2] == 3)}>",
+                     "frac": achieved / peak, "traffic": traffic, "kernel": kname,
                      "peak_kind": peak_kind,
                      "bytes_per_particle_step": BYTES_PER_PARTICLE_STEP},
+        # the same kernel against the measured FP32 FMA rate (its arithmetic)
+        "roofline_alu": alu,
+        "peaks_measured": peaks,
         "e2e": e2e,
         # per step: the persistent MD launch and the f_eq stage's three
         # (moments and lambda, WSG terms split over CTAs, the rest)
@@ -483,26 +548,113 @@ def run_ours(args):
         dist.destroy_process_group()
 
 
-def _oracle_sample(reps, nsteps):
-    """Runs the oracle over the given replicas of the ensemble; returns
+def measured_alu_peaks(mdlg):
+    """FP32 and FP64 fused multiply-add throughput of this GPU, measured now
+    (mdlg_fma_peak: the full resident grid, 8 independent chains a thread)."""
+    f32, _ = mdlg.fma_peak(0, 1 << 22)
+    f64, _ = mdlg.fma_peak(1, 1 << 16)
+    return {"fp32_tflops": f32 / 1e12, "fp64_tflops": f64 / 1e12,
+            "how": "mdlg_fma_peak: FFMA/DFMA chains over the full resident grid, CUDA events"}
+
+
+def _equal_accuracy(mdlg, torch, windows=32, target=1e-4):
+    """Time each path needs to measure P0 (the zero-displacement class of
+    f_eq, Eq. theory_feq) to the same standard error at the same (phi, T,
+    dt_lg, dx): phi = 0.0784, T = 20, dt_lg = 0.2 (400 steps of 5e-4), dx ~ 1.
+    Batched FP32: 64 replicas of 16,384 particles (one launch, the autotuned
+    engine); error of the replica mean from the spread over replicas.  Plain
+    FP64: one system of 262,144 particles; error by batch means over the
+    windows.  Both sample `windows` windows after 2,000 untimed steps; the
+    time to reach `target` scales the timed run by (sigma / target)^2."""
+    from paper_2101_01160_gb300 import inputs
+
+    c0 = (2 * W + 1) ** 2 // 2
+    out = {"target_sigma_p0": target, "windows": windows, "phi": PHI1, "T": T1, "dt_lg": 0.2}
+    neq = 2000
+
+    def timed(sysm, steps):
+        sysm.step(neq)
+        sysm.sync()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        sysm.step(steps)
+        e1.record()
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) * 1e-3
+
+    # batched FP32
+    R, n = 64, 16_384
+    L = inputs.box_length(n, PHI1)
+    states = [inputs.lattice_gas_state(n, L, T1, seed=5000 + r) for r in range(R)]
+    cat = [np.concatenate([getattr(st, f) for st in states]) for f in ("x", "y", "vx", "vy")]
+    p = mdlg.make_params(n, L, dt=DT, precision=mdlg.MD_FP32_CELLOFF, W=W, n_equil=neq, lg_every=(EVERY,),
+                         lx=(int(round(L)),), skin=SKIN)
+    s = mdlg.System([p] * R, *cat)
+    shape = s.autotune(50)
+    s.close()
+    s = mdlg.System([p] * R, *cat)
+    s.tune(*shape)
+    t = timed(s, windows * EVERY)
+    p0 = np.array([s.feq_measured(r, 0, 0)[0][c0] for r in range(R)])
+    s.close()
+    sig = float(p0.std(ddof=1) / np.sqrt(R))
+    out["batched_fp32"] = {"replicas": R, "n": n, "seconds": t, "p0": float(p0.mean()), "sigma_p0": sig,
+                           "seconds_to_target": t * (sig / target) ** 2, "launch_shape": list(shape)}
+    # plain FP64
+    L1 = inputs.box_length(N1, PHI1)
+    st = inputs.lattice_gas_state(N1, L1, T1, seed=1000)
+    p = mdlg.make_params(N1, L1, dt=DT, precision=mdlg.MD_FP64, W=W, n_equil=neq, lg_every=(EVERY,),
+                         lx=(int(round(L1)),))
+    s = mdlg.System(p, st.x, st.y, st.vx, st.vy)
+    s.autotune(50)
+    t = timed(s, windows * EVERY)
+    P, se, _ = s.feq_measured(0, 0, 0)
+    s.close()
+    sig = float(se[c0])
+    out["plain_fp64"] = {"n": N1, "seconds": t, "p0": float(P[c0]), "sigma_p0": sig,
+                         "seconds_to_target": t * (sig / target) ** 2}
+    out["fp64_over_fp32_time"] = out["plain_fp64"]["seconds_to_target"] / out["batched_fp32"]["seconds_to_target"]
+    return out
+
+
+SAMPLE_REPS = list(range(0, N_REP, 16))     # 16 replicas spread over the draw order
+
+
+def _oracle_threads(reps, nsteps, threads):
+    """The oracle over the given replicas of the ensemble, one replica per
+    host thread at a time (the C oracle runs with the GIL released); returns
     (particle-steps, seconds)."""
+    from concurrent.futures import ThreadPoolExecutor
+
     from oracle import oracle
 
-    ens = ensemble(reps=reps)
-    t0 = time.perf_counter()
-    ps = 0
-    for (n, L, _, _, st) in ens:
+    ens = sorted(ensemble(reps=reps), key=lambda e: -e[0])   # largest first: fuller threads
+    oracle.lib()
+
+    def one(e):
+        n, L, _, _, st = e
         oracle.md_run(st.x, st.y, st.vx, st.vy, L, DT, nsteps, every=[EVERY], lx=[int(round(L))], W=W)
-        ps += n * nsteps
+        return n * nsteps
+
+    t0 = time.perf_counter()
+    with ThreadPoolExecutor(max_workers=threads) as ex:
+        ps = sum(ex.map(one, ens))
     return ps, time.perf_counter() - t0
 
 
+def _sample_desc(reps, nsteps, threads):
+    n = sum(e[0] for e in ensemble(reps=reps))
+    return (f"replicas {reps} of the batched ensemble ({n} particles), {nsteps} MD steps each "
+            f"(one sampling window), FP64 C oracle, {threads} host threads, one replica per thread at a time")
+
+
 def cpu_baseline():
-    reps = list(range(0, N_REP, 16))           # 16 replicas spread over the draw order
-    ps, dt = _oracle_sample(reps, MD_PER_STEP)
-    return {"value": ps / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": f"replicas {reps} of the batched ensemble, {MD_PER_STEP} MD steps each "
-                      f"(one sampling window), FP64 C oracle, single thread"}
+    cores = os.cpu_count() or 1
+    ps, dt = _oracle_threads(SAMPLE_REPS, MD_PER_STEP, cores)
+    ps1, dt1 = _oracle_threads(SAMPLE_REPS[:2], MD_PER_STEP, 1)
+    return {"value": ps / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": _sample_desc(SAMPLE_REPS, MD_PER_STEP, cores), "cpu_model": _cpu_model(),
+            "single_thread": {"value": ps1 / dt1, "sample": _sample_desc(SAMPLE_REPS[:2], MD_PER_STEP, 1)}}
 
 
 def run_reference(args):
@@ -511,26 +663,27 @@ def run_reference(args):
     ws, rank, _ = sharding.world()
     if rank != 0:
         return
-    reps = [0, 128]
+    cores = os.cpu_count() or 1
     for _ in range(args.warmup):
-        _oracle_sample(reps, 100)
+        _oracle_threads(SAMPLE_REPS, MD_PER_STEP // 4, cores)
     ps_tot, tot = 0, 0.0
     for _ in range(args.steps):
-        ps, dt = _oracle_sample(reps, 100)
+        ps, dt = _oracle_threads(SAMPLE_REPS, MD_PER_STEP, cores)
         ps_tot += ps
         tot += dt
     value = ps_tot / tot
     ms = tot / args.steps * 1e3
-    sample = (f"replicas {reps} of the batched ensemble, 100 MD steps per step, sampling every "
-              f"{EVERY} steps; FP64 C oracle, single thread")
+    n_sample = sum(e[0] for e in ensemble(reps=SAMPLE_REPS))
     print(json.dumps({
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
         "config": {"workload": WORKLOAD, "n_particles": _ensemble_particles(),
-                   "md_steps_per_step": MD_PER_STEP, "parallelism": "one host core"},
-        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
-                         "sample": sample},
+                   "md_steps_per_step": MD_PER_STEP, "parallelism": f"{cores} host threads",
+                   "sample": {"replicas": SAMPLE_REPS, "n_particles": n_sample,
+                              "md_steps_per_step": MD_PER_STEP}},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                         "sample": _sample_desc(SAMPLE_REPS, MD_PER_STEP, cores), "cpu_model": _cpu_model()},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }), flush=True)
 
