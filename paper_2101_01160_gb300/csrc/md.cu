@@ -470,6 +470,8 @@ struct md_system {
     int res_grid = 0;
     size_t res_smem = 0;
     int res_slabs = 0, res_max_g = 0;
+    std::vector<ResJob> res_jobs;     // the plan's slabs, in device order
+    std::vector<double> res_cost;     // measured per-replica slab times of the current plan, if any
 };
 
 namespace {
@@ -552,7 +554,8 @@ struct ResPlan {
 
 static int round_up(long long v, int m) { return (int)((v + m - 1) / m * m); }
 
-int plan_resident(const std::vector<RepDev> &all, int grid, size_t avail, ResPlan &P) {
+int plan_resident(const std::vector<RepDev> &all, int grid, size_t avail, ResPlan &P,
+                  const std::vector<double> *measured = nullptr) {
     struct Rep {
         int r, g, p_cap, h_cap;
         double cost;
@@ -577,6 +580,8 @@ int plan_resident(const std::vector<RepDev> &all, int grid, size_t avail, ResPla
             const long long e_need = (long long)std::ceil(1.8 * cbar * p_cap) + 256;
             if (res_slab_bytes(p_cap, h_cap, (int)std::min<long long>(e_need, 1 << 30)) > avail) continue;
             best = Rep{r, g, p_cap, h_cap, pmax * (40.0 + 14.0 * cbar) + (g > 1 ? 4000.0 : 0.0)};
+            // a measured time of the replica's slabs replaces the model
+            if (measured && r < (int)measured->size() && (*measured)[r] > 0.0) best.cost = (*measured)[r];
             break;
         }
         if (best.g == 0)
@@ -650,22 +655,25 @@ void free_resident(md_system *s) {
     s->res_grid = 0;
 }
 
-int configure_resident(md_system *s) {
+int configure_resident(md_system *s, const std::vector<double> *measured = nullptr) {
     if (s->prec != MD_FP32_CELLOFF) return fail(MD_E_ARG, "the resident engine (staging 4) is FP32 only");
-    int optin = 0;
+    int optin = 0, per_sm = 0;
     MD_CUDA_TRY(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, s->dev));
+    MD_CUDA_TRY(cudaDeviceGetAttribute(&per_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, s->dev));
     cudaFuncAttributes fa{};
     MD_CUDA_TRY(cudaFuncGetAttributes(&fa, k_md_resident));
-    const size_t smem = (size_t)optin - fa.sharedSizeBytes;
+    // RES_CTAS_PER_SM CTAs share an SM's shared memory (1 KB of it is
+    // reserved per CTA)
+    const size_t smem = std::min((size_t)optin, (size_t)per_sm / RES_CTAS_PER_SM - 1024) - fa.sharedSizeBytes;
     const size_t hb = smem_hist_bytes(s->n_lg, s->n_dx, s->nb);
     if (hb + 4096 > smem) return fail(MD_E_LIMIT, "resident engine: histograms leave no shared memory");
     MD_CUDA_TRY(cudaFuncSetAttribute(k_md_resident, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     int occ = 0;
     MD_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_md_resident, RES_THREADS, smem));
-    if (occ < 1) return fail(MD_E_CUDA, "resident kernel does not fit on an SM");
-    const int grid = s->nsm;
+    if (occ < RES_CTAS_PER_SM) return fail(MD_E_CUDA, "resident kernel: %d of %d CTAs fit on an SM", occ, RES_CTAS_PER_SM);
+    const int grid = s->nsm * RES_CTAS_PER_SM;
     ResPlan P;
-    int rc = plan_resident(s->reps, grid, smem - hb, P);
+    int rc = plan_resident(s->reps, grid, smem - hb, P, measured);
     if (rc) return rc;
     MD_CUDA_TRY(cudaStreamSynchronize(s->st));   // no launch may still use the old buffers
     free_resident(s);
@@ -690,6 +698,7 @@ int configure_resident(md_system *s) {
     A((void **)&D.mig_n, sizeof(int32_t) * grid * 2);
     A((void **)&D.slab_n, sizeof(int32_t) * grid);
     A((void **)&D.gbar, sizeof(unsigned) * 2 * (size_t)s->nrep);
+    A((void **)&D.job_ns, sizeof(unsigned long long) * std::max<size_t>(1, P.jobs.size()));
     if (rc) {
         free_resident(s);
         return rc;
@@ -705,6 +714,8 @@ int configure_resident(md_system *s) {
     s->res_smem = smem;
     s->res_slabs = P.slabs;
     s->res_max_g = P.max_g;
+    s->res_jobs = P.jobs;
+    s->res_cost = measured ? *measured : std::vector<double>();
     s->engine = 1;   // the global engine keeps its own launch shape for its other uses
     return MD_OK;
 }
@@ -1427,6 +1438,7 @@ int feq_batch(md_system *s, int32_t lg, int32_t dxi, int32_t symmetrize, double 
 namespace {
 std::mutex g_tune_mu;
 std::map<std::tuple<int, int, int, int>, std::tuple<int, int, int>> g_tune_cache;
+std::map<std::tuple<int, int, int, int>, std::vector<double>> g_tune_costs;   // resident slab times
 }
 
 int md_autotune(md_system *s, int64_t steps_per_trial, int32_t *best3) {
@@ -1438,8 +1450,12 @@ int md_autotune(md_system *s, int64_t steps_per_trial, int32_t *best3) {
         std::lock_guard<std::mutex> lk(g_tune_mu);
         auto it = g_tune_cache.find(key);
         if (it != g_tune_cache.end()) {
-            int rc = configure_launch(s, std::get<0>(it->second), std::get<1>(it->second),
-                                      std::get<2>(it->second));
+            auto ic = g_tune_costs.find(key);
+            int rc = std::get<2>(it->second) == 4 && ic != g_tune_costs.end() && !ic->second.empty() &&
+                             (int)ic->second.size() == s->nrep
+                         ? configure_resident(s, &ic->second)
+                         : configure_launch(s, std::get<0>(it->second), std::get<1>(it->second),
+                                            std::get<2>(it->second));
             if (rc) return rc;
             if (best3) {
                 best3[0] = std::get<0>(it->second);
@@ -1477,10 +1493,15 @@ int md_autotune(md_system *s, int64_t steps_per_trial, int32_t *best3) {
                     bs = st;
                 }
             }
-    // the shared-memory-resident engine (batched FP32 ensembles)
+    // the shared-memory-resident engine (batched FP32 ensembles): a trial
+    // with the modelled slab costs, then one with the schedule re-planned
+    // from the slabs' measured times (the per-replica work split this
+    // tunes; no result depends on the schedule)
+    std::vector<double> res_cost;
     if (rc == MD_OK && s->prec == MD_FP32_CELLOFF && s->nrep >= 2 && configure_launch(s, 256, 1, 4) == MD_OK) {
-        rc = md_step(s, steps_per_trial);
-        if (rc == MD_OK) {
+        for (int trial = 0; trial < 2 && rc == MD_OK; ++trial) {
+            rc = md_step(s, steps_per_trial);
+            if (rc) break;
             cudaEventRecord(e0, s->st);
             rc = md_step(s, steps_per_trial);
             cudaEventRecord(e1, s->st);
@@ -1492,6 +1513,19 @@ int md_autotune(md_system *s, int64_t steps_per_trial, int32_t *best3) {
                 bb = 256;
                 bp = 1;
                 bs = 4;
+                res_cost.clear();
+                if (trial == 1) res_cost = s->res_cost;
+            }
+            if (trial == 0 && rc == MD_OK) {
+                // per replica: the longest of its slabs in the last launch
+                std::vector<unsigned long long> ns(s->res_jobs.size());
+                if (cudaMemcpy(ns.data(), s->rd.job_ns, sizeof(unsigned long long) * ns.size(),
+                               cudaMemcpyDeviceToHost) != cudaSuccess)
+                    break;
+                std::vector<double> cost(s->nrep, 0.0);
+                for (size_t j = 0; j < ns.size(); ++j)
+                    cost[s->res_jobs[j].rep] = std::max(cost[s->res_jobs[j].rep], (double)ns[j]);
+                if (configure_resident(s, &cost) != MD_OK) break;
             }
         }
     }
@@ -1500,11 +1534,12 @@ int md_autotune(md_system *s, int64_t steps_per_trial, int32_t *best3) {
     if (rc) return rc;
     rc = sync_status(s);
     if (rc) return rc;
-    rc = configure_launch(s, bb, bp, bs);
+    rc = bs == 4 && !res_cost.empty() ? configure_resident(s, &res_cost) : configure_launch(s, bb, bp, bs);
     if (rc) return rc;
     {
         std::lock_guard<std::mutex> lk(g_tune_mu);
         g_tune_cache[key] = std::make_tuple(bb, bp, bs);
+        g_tune_costs[key] = res_cost;
     }
     if (best3) {
         best3[0] = bb;

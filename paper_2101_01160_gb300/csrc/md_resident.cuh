@@ -31,6 +31,7 @@
 namespace mdlg {
 
 constexpr int RES_THREADS = 1024;
+constexpr int RES_CTAS_PER_SM = 1;   // row slabs of wide dense replicas need a whole SM's shared memory
 constexpr int RES_NCC = 2048;      // coarse cells of the list-building grid
 constexpr int RES_PCAP = 8192;     // own particles of one slab (index + 2 halo < 2^14)
 constexpr int RES_MAXLIST = 255;   // neighbours of one particle (u8 row counts)
@@ -56,6 +57,7 @@ struct ResDev {
     int32_t *mig_n;           // [grid][2]
     int32_t *slab_n;          // [grid]: particles of the slab at write-back
     unsigned *gbar;           // [nrep][2]: gang barrier arrivals, generation
+    unsigned long long *job_ns;   // [jobs]: each slab's time from its first barrier to its store
     int32_t hmax;
     int32_t smem_bytes;       // dynamic shared memory of the launch
 };
@@ -146,7 +148,7 @@ __device__ __forceinline__ void res_fail(int *status, int flag) { atomicOr(statu
 extern __shared__ __align__(16) unsigned char res_smem[];
 
 struct Slab {
-    uint32_t o_off[2], o_hoff, o_vel, o_cell, o_id, o_lst, o_rend, o_bidx, o_ent;
+    uint32_t o_off[2], o_hoff, o_vel, o_cell, o_id, o_lst, o_rend, o_bidx, o_bpos, o_ent;
     int e_cap;
     __device__ __forceinline__ float2 *off(int b) const { return reinterpret_cast<float2 *>(res_smem + o_off[b]); }
     __device__ __forceinline__ float2 *hoff() const { return reinterpret_cast<float2 *>(res_smem + o_hoff); }
@@ -156,12 +158,16 @@ struct Slab {
     __device__ __forceinline__ uint32_t *lst() const { return reinterpret_cast<uint32_t *>(res_smem + o_lst); }
     __device__ __forceinline__ uint16_t *rend() const { return reinterpret_cast<uint16_t *>(res_smem + o_rend); }
     __device__ __forceinline__ uint16_t *bidx() const { return reinterpret_cast<uint16_t *>(res_smem + o_bidx); }
+    // per own particle: side << 15 | position in that side's boundary set, or
+    // RES_NOB (not in the first or the last row)
+    __device__ __forceinline__ uint16_t *bpos() const { return reinterpret_cast<uint16_t *>(res_smem + o_bpos); }
     __device__ __forceinline__ uint16_t *ent() const { return reinterpret_cast<uint16_t *>(res_smem + o_ent); }
     // build scratch in the spare own-offset buffer of cur
     __device__ __forceinline__ unsigned char *scratch(int cur) const { return res_smem + o_off[cur ^ 1]; }
 };
 
 constexpr uint32_t RES_IDX = (1u << 14) - 1u;
+constexpr uint16_t RES_NOB = 0xffffu;
 
 __host__ __device__ inline size_t res_off_bytes(int p_cap, int h_cap) {
     // an own-offset buffer, large enough to hold the build scratch
@@ -177,7 +183,7 @@ __host__ __device__ inline size_t res_slab_bytes(int p_cap, int h_cap, int e_cap
            align16((size_t)p_cap * sizeof(float2)) + align16(ph * sizeof(uint32_t)) +
            align16(ph * sizeof(int32_t)) + align16(((size_t)p_cap + 1) * sizeof(uint32_t)) +
            align16((size_t)p_cap * sizeof(uint16_t)) + align16(2 * (size_t)h_cap * sizeof(uint16_t)) +
-           align16((size_t)e_cap * sizeof(uint16_t));
+           align16((size_t)p_cap * sizeof(uint16_t)) + align16((size_t)e_cap * sizeof(uint16_t));
 }
 
 __device__ inline Slab res_layout(uint32_t base, int p_cap, int h_cap, size_t avail) {
@@ -194,6 +200,7 @@ __device__ inline Slab res_layout(uint32_t base, int p_cap, int h_cap, size_t av
     L.o_lst = p; p += (uint32_t)align16(((size_t)p_cap + 1) * sizeof(uint32_t));
     L.o_rend = p; p += (uint32_t)align16((size_t)p_cap * sizeof(uint16_t));
     L.o_bidx = p; p += (uint32_t)align16(2 * (size_t)h_cap * sizeof(uint16_t));
+    L.o_bpos = p; p += (uint32_t)align16((size_t)p_cap * sizeof(uint16_t));
     L.o_ent = p;
     const size_t used = (size_t)(p - base);
     L.e_cap = used < avail ? (int)((avail - used) / sizeof(uint16_t)) : 0;
@@ -304,6 +311,8 @@ __device__ bool res_halo_full(const SysDev &S, const ResDev &D, const RepDev &R,
     const int me = blockIdx.x;
     const int rows[2] = {X.J.r0, X.J.r1 - 1};
     bool over = false;
+    for (int i = threadIdx.x; i < X.p; i += RES_THREADS) L.bpos()[i] = RES_NOB;
+    __syncthreads();
     for (int side = 0; side < 2; ++side) {
         int n = 0;
         for (int base = 0; base < X.p; base += RES_THREADS) {
@@ -314,6 +323,7 @@ __device__ bool res_halo_full(const SysDev &S, const ResDev &D, const RepDev &R,
             if (f) {
                 if (at < X.J.h_cap) {
                     L.bidx()[side * X.J.h_cap + at] = (uint16_t)i;
+                    L.bpos()[i] = (uint16_t)((side << 15) | at);
                     const long long gi = ((long long)me * 2 + side) * D.hmax + at;
                     D.halo_ci[gi] = make_uint2(L.cell()[i], (uint32_t)L.id()[i]);
                     D.halo_off[(((long long)me * 2 + side) * 2 + X.par) * D.hmax + at] = L.off(X.cur)[i];
@@ -595,7 +605,8 @@ __device__ bool res_canon_migrate(const SysDev &S, const ResDev &D, const RepDev
 // entry from its tag: the arithmetic of lj_list), then the velocity-Verlet
 // update of kick_drift into the other own-offset buffer.
 __device__ __forceinline__ void res_force_kick(const SysDev &S, const RepDev &R, const float *P, const Slab &L,
-                                               const SlabRun &X, int i, bool first, bool dbg, float &vm, bool &bad) {
+                                               const SlabRun &X, int i, bool first, bool dbg, float2 *pub0,
+                                               float2 *pub1, float &vm, bool &bad) {
     const float2 *off = L.off(X.cur);
     const float2 *hoff = L.hoff();
     const uint16_t *ent = L.ent();
@@ -606,20 +617,32 @@ __device__ __forceinline__ void res_force_kick(const SysDev &S, const RepDev &R,
     const float sys[3] = {-h - oi.y, -oi.y, h - oi.y};
     const uint32_t st = L.lst()[i], en = L.lst()[i + 1];
     const uint32_t re = L.rend()[i];
-    const uint32_t ends[3] = {st + (re & 0xffu), st + (re >> 8), en};
+    const uint32_t e1 = st + (re & 0xffu), e2 = st + (re >> 8);
     float fx = 0.0f, fy = 0.0f;
     double pe_unused = 0.0, fa_unused = 0.0;
-    uint32_t e = st;
+    // batches of RES_U entries: all index and position loads of a batch are
+    // issued before its pair arithmetic (latency hiding); the pairs are
+    // still summed one by one in list order
+    constexpr int RES_U = 4;
+    for (uint32_t e = st; e < en; e += RES_U) {
+        uint32_t v[RES_U];
+        float2 o[RES_U];
 #pragma unroll
-    for (int row = 0; row < 3; ++row) {
-        const float sy = sys[row];
-        for (; e < ends[row]; ++e) {
-            const uint32_t v = ent[e];
-            const int j = (int)(v & RES_IDX);
-            const uint32_t t = v >> 14;
-            const float2 o = j < pc ? off[j] : hoff[j - pc];
-            const float sx = t == 0 ? sx0 : (t == 1 ? sx1 : sx2);
-            lj_pair_acc<float, false>(o.x + sx, o.y + sy, rc2, eps24, sig2, fx, fy, 0.0, pe_unused, fa_unused);
+        for (int u = 0; u < RES_U; ++u) v[u] = e + u < en ? (uint32_t)ent[e + u] : 0u;
+#pragma unroll
+        for (int u = 0; u < RES_U; ++u) {
+            const int j = (int)(v[u] & RES_IDX);
+            o[u] = j < pc ? off[j] : hoff[j - pc];
+        }
+#pragma unroll
+        for (int u = 0; u < RES_U; ++u) {
+            if (e + u < en) {
+                const uint32_t t = v[u] >> 14;
+                const float sx = t == 0 ? sx0 : (t == 1 ? sx1 : sx2);
+                const float sy = e + u < e1 ? sys[0] : (e + u < e2 ? sys[1] : sys[2]);
+                lj_pair_acc<float, false>(o[u].x + sx, o[u].y + sy, rc2, eps24, sig2, fx, fy, 0.0, pe_unused,
+                                          fa_unused);
+            }
         }
     }
     if (dbg) {
@@ -627,6 +650,11 @@ __device__ __forceinline__ void res_force_kick(const SysDev &S, const RepDev &R,
         S.dbg_fy[L.id()[i]] = (double)fy;
     }
     kick_drift<float>(R, oi, L.vel()[i], fx, fy, P[4], P[5], first, P[6], L.off(X.cur ^ 1), L.vel(), i, vm, bad);
+    // a boundary particle's new offset goes straight to the neighbours' halo
+    if (pub0) {
+        const uint16_t b = L.bpos()[i];
+        if (b != RES_NOB) (b >> 15 ? pub1 : pub0)[b & 0x7fffu] = L.off(X.cur ^ 1)[i];
+    }
 }
 
 // Block maximum of v over the CTA into thread 0 (fixed order).
@@ -643,7 +671,7 @@ __device__ __forceinline__ float block_max(float v, float *s_f) {
 
 // ---------------------------------------------------------------- kernel
 // Runs every slab job of this CTA for nsteps steps from step0.
-__global__ void __launch_bounds__(RES_THREADS, 1) k_md_resident(SysDev S, ResDev D, long long step0,
+__global__ void __launch_bounds__(RES_THREADS, RES_CTAS_PER_SM) k_md_resident(SysDev S, ResDev D, long long step0,
                                                                 long long nsteps, int phase_half) {
     __shared__ int s_w[33];
     __shared__ float s_f[32];
@@ -692,6 +720,7 @@ __global__ void __launch_bounds__(RES_THREADS, 1) k_md_resident(SysDev S, ResDev
             return;
         }
         if (!res_halo_full(S, D, R, L, X, my_gen, bar, s_w)) return;
+        const uint64_t t_job = global_ns();   // the gang is together from here on
         if (!res_lists(S, R, L, X, s_w)) return;
         double m2acc[MD_MAX_LG], m4acc[MD_MAX_LG];
         for (long long it = 0; it < nsteps; ++it) {
@@ -714,17 +743,17 @@ __global__ void __launch_bounds__(RES_THREADS, 1) k_md_resident(SysDev S, ResDev
             const bool dbg = S.dbg_fx && it == nsteps - 1;
             float vm = 0.0f;
             bool bad = false;
-            for (int i = tid; i < X.p; i += RES_THREADS) res_force_kick(S, R, s_par, L, X, i, first, dbg, vm, bad);
+            const int nx = X.cur ^ 1, npar = X.par ^ 1;
+            float2 *pub0 = nullptr, *pub1 = nullptr;
+            if (X.J.g > 1) {
+                pub0 = D.halo_off + (((long long)blockIdx.x * 2 + 0) * 2 + npar) * D.hmax;
+                pub1 = D.halo_off + (((long long)blockIdx.x * 2 + 1) * 2 + npar) * D.hmax;
+            }
+            for (int i = tid; i < X.p; i += RES_THREADS)
+                res_force_kick(S, R, s_par, L, X, i, first, dbg, pub0, pub1, vm, bad);
             if (__syncthreads_or(bad) && tid == 0) atomicOr(&C->status, (int)DS_NONFINITE);
             const float m = block_max(vm, s_f);
             if (tid == 0) atomicMax(&S.vmax_rep[(long long)X.J.rep * 3 + s % 3], __float_as_uint(m));
-            // publish the new boundary offsets for the neighbours
-            const int nx = X.cur ^ 1, npar = X.par ^ 1;
-            if (X.J.g > 1)
-                for (int side = 0; side < 2; ++side)
-                    for (int t = tid; t < X.nb[side]; t += RES_THREADS)
-                        D.halo_off[(((long long)blockIdx.x * 2 + side) * 2 + npar) * D.hmax + t] =
-                            L.off(nx)[L.bidx()[side * X.J.h_cap + t]];
             if (!gang_sync(bar, X.J.g, my_gen, &C->status, S.timeout_ns)) return;
             if (tid == 0) {
                 const unsigned v = *(volatile unsigned *)&S.vmax_rep[(long long)X.J.rep * 3 + s % 3];
@@ -810,6 +839,7 @@ __global__ void __launch_bounds__(RES_THREADS, 1) k_md_resident(SysDev S, ResDev
             __syncthreads();
         }
         if (!res_store(S, D, R, L, X, set ^ 1, my_gen, bar)) return;
+        if (tid == 0) D.job_ns[jb] = global_ns() - t_job;
         if (tid == 0 && X.J.k == 0) S.disp_rep[X.J.rep] = s_disp;
         __syncthreads();
     }
