@@ -248,6 +248,26 @@ int md_get_state(md_system *s, double *x, double *y, double *vx, double *vy);
 int md_set_state(md_system *s, const double *x, const double *y, const double *vx,
                  const double *vy);
 
+/* Exact checkpoint of a system (no counterpart in the paper): everything
+ * that decides its future trajectory and statistics -- step counter,
+ * half-step flag, displacement bounds, the particle state slot by slot
+ * (cells, offsets, velocities, ids), the sampling snapshots, the integer
+ * histograms of every error-bar block, the overflow counts and the FP64
+ * moment partials.  md_checkpoint_bytes gives the size; md_checkpoint_save
+ * writes it to host memory `buf` (synchronises); md_checkpoint_load
+ * restores it into a system created by md_init / md_init_batch with the
+ * same parameters (any initial state; MD_E_ARG for a checkpoint of other
+ * sizes) and synchronises.  Running k steps, saving, loading into a fresh
+ * system and running m more steps gives the same bits as k + m steps
+ * straight: positions, velocities, snapshots, histograms and overflow on
+ * either engine, the FP64 moment sums too on the global engine (the
+ * resident engine sums a slab's moment terms in its slot order, which a
+ * load resets, so their last bits may differ).  The buffer format is that
+ * of this library build only. */
+int md_checkpoint_bytes(md_system *s, int64_t *bytes);
+int md_checkpoint_save(md_system *s, void *buf);
+int md_checkpoint_load(md_system *s, const void *buf);
+
 /* Raw current positions in the snapshot encoding, particle-id order:
  * cell (linear cy*ncell+cx), offsets as float (MD_FP32_CELLOFF) or double
  * (MD_FP64).  Device outputs.  Synchronises. */
@@ -291,6 +311,27 @@ int md_hist_raw(md_system *s, int32_t rep, int32_t lg, int32_t dxi, int64_t *his
  * the device in FP64; outputs are host memory.  Synchronises. */
 int feq_measured(md_system *s, int32_t rep, int32_t lg, int32_t dxi, int32_t symmetrize,
                  double *P_out, double *stderr_out, md_feq_stats *stats);
+
+/* The integer histogram of (rep, lg, dxi) per error-bar block: hist (host,
+ * int32, [MD_NBLK][(2W+1)^2]) and wblk (host, int64, [MD_NBLK]) the windows
+ * each block holds.  Synchronises. */
+int md_hist_blocks(md_system *s, int32_t rep, int32_t lg, int32_t dxi, int32_t *hist, int64_t *wblk);
+
+/* Block-bootstrap standard error of the measured equilibrium (Eq.
+ * theory_feq as feq_measured normalises it; the paper's averages over
+ * iterations come from a finite run) for every replica: the error-bar
+ * blocks of windows holding data are resampled with replacement, as many
+ * draws as used blocks, n_resamples times (2 .. 2^20); each resample's P_i
+ * is its drawn counts over n * its drawn windows (symmetric-set averaged if
+ * symmetrize != 0); sigma_out[r*(2W+1)^2 + i] is the sample standard
+ * deviation of P_i over the resamples (divisor n_resamples - 1).  Draws:
+ * SplitMix64 (Steele, Lea and Flood 2014) as a counter-based generator,
+ * draw c = ((r * 2^20 + b) * 64 + k) of `seed` for slot k of resample b:
+ * the output function of seed + (c + 1) * 0x9e3779b97f4a7c15, block index
+ * = (draw >> 32) * used >> 32.  sigma_out: host (synchronises) or device
+ * (asynchronous on the stream). */
+int feq_bootstrap(md_system *s, int32_t lg, int32_t dxi, int32_t symmetrize, int32_t n_resamples, uint64_t seed,
+                  double *sigma_out);
 
 /* The whole f_eq stage for every replica in one launch (no host round
  * trip): per replica r, out[r*(3*nb+16) + ...] holds

@@ -40,6 +40,9 @@
  *                                PDF, Eqs. (poisson_v2) and (p_wsg_one)
  *   or_kl_terms                  element-wise K(X_i) of Eq. (k_Xi)
  *   or_symmetrize                the symmetric-set averaging of Sec. 5
+ *   or_bootstrap_feq             block-bootstrap standard error of the
+ *                                measured equilibrium (the run averages of
+ *                                Sec. 2 are finite), draws by SplitMix64
  *   or_forces_brute              the Lennard-Jones force of Sec. 4, all
  *                                pairs, minimum image, cutoff rc, potential
  *                                shifted to zero at rc (force not shifted)
@@ -435,6 +438,99 @@ void or_symmetrize(const double *P, int32_t W, double *out)
                 }
             out[iy * side + ix] = s / (double)m;
         }
+}
+
+/* ------------------------------------------------------------------------ */
+/* Statistical error of the measured equilibrium by the block bootstrap (the
+ * averages over iterations of Sec. 2 are estimated from a finite run): the
+ * error-bar blocks of windows that hold data are resampled with replacement,
+ * nblk_used draws per resample, and each resample's P_i = sum of the drawn
+ * blocks' counts / (n * drawn windows) (optionally averaged over the
+ * symmetric set of i, as or_symmetrize does); sigma_i is the sample
+ * standard deviation of P_i over the B resamples (divisor B - 1).
+ *
+ * Draws come from SplitMix64 (Steele, Lea and Flood, "Fast splittable
+ * pseudorandom number generators", OOPSLA 2014) used as a counter-based
+ * generator: draw number c of a stream gives the output function applied
+ * to seed + (c + 1) * 0x9e3779b97f4a7c15; block index = the draw's top 32
+ * bits times nblk_used, shifted right by 32.  The draw of resample b, slot k
+ * of replica rep has c = ((rep * 2^20 + b) * 64 + k). */
+uint64_t or_splitmix64(uint64_t seed, uint64_t c)
+{
+    uint64_t z = seed + (c + 1u) * 0x9e3779b97f4a7c15ull;
+    z = (z ^ (z >> 30)) * 0xbf58476d1ce4e5b9ull;
+    z = (z ^ (z >> 27)) * 0x94d049bb133111ebull;
+    return z ^ (z >> 31);
+}
+
+int or_bootstrap_feq(const int64_t *hist, const int64_t *wblk, int32_t nblk, int32_t W, double n,
+                     int32_t sym, int32_t B, uint64_t seed, int32_t rep, double *sigma)
+{
+    int32_t side = 2 * W + 1, nb = side * side;
+    int32_t used[64];
+    int32_t nu = 0;
+    if (nblk > 64 || B < 2) return -1;
+    for (int32_t k = 0; k < nblk; ++k)
+        if (wblk[k] > 0) used[nu++] = k;
+    double *P = (double *)malloc(sizeof(double) * (size_t)B * (size_t)nb);
+    int64_t *Hs = (int64_t *)malloc(sizeof(int64_t) * (size_t)nb);
+    if (!P || !Hs) {
+        free(P);
+        free(Hs);
+        return -2;
+    }
+    for (int32_t i = 0; i < nb; ++i) sigma[i] = 0.0;
+    if (nu == 0) {
+        free(P);
+        free(Hs);
+        return 0;
+    }
+    for (int32_t b = 0; b < B; ++b) {
+        int64_t wsum = 0;
+        for (int32_t i = 0; i < nb; ++i) Hs[i] = 0;
+        for (int32_t k = 0; k < nu; ++k) {
+            uint64_t c = (((uint64_t)rep << 20) + (uint64_t)b) * 64u + (uint64_t)k;
+            uint64_t r = or_splitmix64(seed, c);
+            int32_t u = used[(int32_t)(((r >> 32) * (uint64_t)nu) >> 32)];
+            wsum += wblk[u];
+            for (int32_t i = 0; i < nb; ++i) Hs[i] += hist[(int64_t)u * nb + i];
+        }
+        for (int32_t iy = 0; iy < side; ++iy)
+            for (int32_t ix = 0; ix < side; ++ix) {
+                int64_t h = 0;
+                int32_t m = 0;
+                if (sym) {
+                    int32_t a = abs(ix - W), bb = abs(iy - W);
+                    int32_t lo = a < bb ? a : bb, hi = a < bb ? bb : a;
+                    for (int32_t jy = 0; jy < side; ++jy)
+                        for (int32_t jx = 0; jx < side; ++jx) {
+                            int32_t c2 = abs(jx - W), d2 = abs(jy - W);
+                            int32_t lo2 = c2 < d2 ? c2 : d2, hi2 = c2 < d2 ? d2 : c2;
+                            if (lo2 == lo && hi2 == hi) {
+                                h += Hs[jy * side + jx];
+                                ++m;
+                            }
+                        }
+                } else {
+                    h = Hs[iy * side + ix];
+                    m = 1;
+                }
+                P[(int64_t)b * nb + iy * side + ix] = (double)h / ((double)m * n * (double)wsum);
+            }
+    }
+    for (int32_t i = 0; i < nb; ++i) {
+        double mean = 0.0, ss = 0.0;
+        for (int32_t b = 0; b < B; ++b) mean += P[(int64_t)b * nb + i];
+        mean /= (double)B;
+        for (int32_t b = 0; b < B; ++b) {
+            double d = P[(int64_t)b * nb + i] - mean;
+            ss += d * d;
+        }
+        sigma[i] = sqrt(ss / (double)(B - 1));
+    }
+    free(P);
+    free(Hs);
+    return 0;
 }
 
 /* ------------------------------------------------------------------------ */

@@ -89,6 +89,10 @@ def _declare(L):
     L.or_pdf_wsg_bins.restype = None
     L.or_symmetrize.argtypes = [P, I32, P]
     L.or_symmetrize.restype = None
+    L.or_splitmix64.argtypes = [C.c_uint64, C.c_uint64]
+    L.or_splitmix64.restype = C.c_uint64
+    L.or_bootstrap_feq.argtypes = [P, P, I32, I32, D, I32, I32, C.c_uint64, I32, P]
+    L.or_bootstrap_feq.restype = C.c_int
     L.or_lj_pair.argtypes = [D, D, D, D, P]
     L.or_lj_pair.restype = D
     L.or_forces_brute.argtypes = [I64, P, P, D, D, D, D, P, P, P, P]
@@ -252,6 +256,22 @@ def symmetrize(P_, W):
     P_ = _f64(P_)
     out = np.zeros_like(P_)
     lib().or_symmetrize(_p(P_), W, _p(out))
+    return out
+
+
+def splitmix64(seed, c):
+    return int(lib().or_splitmix64(seed & (2 ** 64 - 1), c & (2 ** 64 - 1)))
+
+
+def bootstrap_feq(hist_blocks, wblk, W, n, sym=False, B=200, seed=0, rep=0):
+    """Block-bootstrap standard error of the measured P_i (or_bootstrap_feq):
+    hist_blocks int64 [nblk, (2W+1)^2], wblk int64 [nblk] windows per block."""
+    h = np.ascontiguousarray(hist_blocks, dtype=np.int64)
+    w = np.ascontiguousarray(wblk, dtype=np.int64)
+    out = np.zeros((2 * W + 1) ** 2)
+    rc = lib().or_bootstrap_feq(_p(h), _p(w), len(w), W, float(n), int(sym), int(B), seed & (2 ** 64 - 1), rep,
+                                _p(out))
+    assert rc == 0, rc
     return out
 
 

@@ -431,6 +431,90 @@ __global__ void __launch_bounds__(FEQB_THREADS) k_feq_batch(FeqBatchArgs A, cons
     if (tid == 0) out[3 * A.nb + 13] = s_a[0];
 }
 
+// ---------------------------------------------------------------- bootstrap
+// Block-bootstrap standard error of the measured equilibrium of every
+// replica: the error-bar blocks of windows that hold data are resampled with
+// replacement (as many draws as used blocks), each resample's P_i = drawn
+// counts / (n * drawn windows), optionally averaged over i's symmetric set;
+// sigma_i = sample standard deviation over the B resamples (divisor B - 1).
+// Draw c of replica rep is SplitMix64 (Steele, Lea and Flood 2014) used as a
+// counter-based generator: the output function of seed + (c + 1) * gamma,
+// gamma = 0x9e3779b97f4a7c15, c = ((rep * 2^20 + b) * 64 + k) for slot k of
+// resample b; block = (draw >> 32) * used >> 32.  One CTA per replica, one
+// thread per class; every thread walks the resamples in order.
+__device__ __forceinline__ uint64_t splitmix64(uint64_t seed, uint64_t c) {
+    uint64_t z = seed + (c + 1u) * 0x9e3779b97f4a7c15ull;
+    z = (z ^ (z >> 30)) * 0xbf58476d1ce4e5b9ull;
+    z = (z ^ (z >> 27)) * 0x94d049bb133111ebull;
+    return z ^ (z >> 31);
+}
+
+struct BootArgs {
+    const RepDev *reps;
+    const int32_t *hist;   // [nrep][n_lg][n_dx][MD_NBLK][nb]
+    int n_lg, n_dx, lg, dxi, nb, W, sym, B;
+    uint64_t seed;
+    long long wblk[MD_NBLK];
+    double *sigma;         // [nrep][nb]
+};
+
+__global__ void k_feq_bootstrap(BootArgs A) {
+    __shared__ int s_used[MD_NBLK];
+    __shared__ int s_nu;
+    const int r = blockIdx.x;
+    if (threadIdx.x == 0) {
+        int nu = 0;
+        for (int k = 0; k < MD_NBLK; ++k)
+            if (A.wblk[k] > 0) s_used[nu++] = k;
+        s_nu = nu;
+    }
+    __syncthreads();
+    const int nu = s_nu, side = 2 * A.W + 1;
+    const double n = (double)A.reps[r].n;
+    const int32_t *h = A.hist + ((((long long)r * A.n_lg + A.lg) * A.n_dx + A.dxi) * MD_NBLK) * A.nb;
+    for (int i = threadIdx.x; i < A.nb; i += blockDim.x) {
+        int mem[8], nm = 0;
+        if (A.sym) {
+            const int a = abs(i % side - A.W), b = abs(i / side - A.W);
+            const int lo = min(a, b), hi = max(a, b);
+            for (int j = 0; j < A.nb && nm < 8; ++j) {
+                const int c = abs(j % side - A.W), d = abs(j / side - A.W);
+                if (min(c, d) == lo && max(c, d) == hi) mem[nm++] = j;
+            }
+        } else {
+            mem[nm++] = i;
+        }
+        double sig = 0.0;
+        if (nu > 0) {
+            // two passes over the resamples (mean, then squared deviations),
+            // each resample recomputed from its draws
+            double mean = 0.0, ss = 0.0;
+            for (int pass = 0; pass < 2; ++pass) {
+                for (int b = 0; b < A.B; ++b) {
+                    long long hs = 0, ws = 0;
+                    for (int k = 0; k < nu; ++k) {
+                        const uint64_t c = (((uint64_t)r << 20) + (uint64_t)b) * 64u + (uint64_t)k;
+                        const uint64_t x = splitmix64(A.seed, c);
+                        const int u = s_used[(int)(((x >> 32) * (uint64_t)nu) >> 32)];
+                        ws += A.wblk[u];
+                        for (int m = 0; m < nm; ++m) hs += h[(long long)u * A.nb + mem[m]];
+                    }
+                    const double P = (double)hs / ((double)nm * n * (double)ws);
+                    if (pass == 0) {
+                        mean += P;
+                    } else {
+                        const double d = P - mean;
+                        ss = __dadd_rn(ss, __dmul_rn(d, d));   // rounded as the plain definition
+                    }
+                }
+                if (pass == 0) mean /= (double)A.B;
+            }
+            sig = sqrt(ss / (double)(A.B - 1));
+        }
+        A.sigma[(long long)r * A.nb + i] = sig;
+    }
+}
+
 }  // namespace mdlg
 
 using namespace mdlg;
@@ -1177,6 +1261,108 @@ int md_tune(md_system *s, int32_t block_threads, int32_t per_thread, int32_t sta
     return configure_launch(s, block_threads, per_thread, staging);
 }
 
+// ---- checkpoint ---------------------------------------------------------------
+// Layout of a checkpoint (host memory): header, then the arrays in the order
+// of ckpt_parts.  The state is stored slot by slot in the current set, sorted
+// by cell and by id inside a cell (a resident launch's order is sorted
+// first), so a load followed by a sort that moves nothing restores the slot
+// order, and with it every later force sum and moment partial.
+struct CkptHeader {
+    uint64_t magic;
+    int64_t step, ntot, n_rebuilds;
+    int32_t version, prec, nrep, nslots, n_lg, n_dx, nb, phase_half;
+};
+constexpr uint64_t CKPT_MAGIC = 0x4d444c4743484b31ull;   // "MDLGCHK1"
+
+struct CkptPart {
+    void *dev;
+    size_t bytes;
+};
+
+static std::vector<CkptPart> ckpt_parts(md_system *s, int set, int cur) {
+    const SysDev &S = s->sd;
+    const size_t vsz = s->prec == MD_FP64 ? sizeof(double2) : sizeof(float2);
+    const size_t ns = (size_t)s->nslots, nlg = (size_t)std::max(1, s->n_lg);
+    const size_t nhist = (size_t)s->nrep * nlg * s->n_dx * MD_NBLK * s->nb;
+    return {{S.cell[set], sizeof(uint32_t) * ns},
+            {S.pid[set], sizeof(int32_t) * ns},
+            {S.vel[set], vsz * ns},
+            {S.pos[set][cur], vsz * ns},
+            {S.disp_rep, sizeof(double) * (size_t)s->nrep},
+            {S.snap_cell, sizeof(uint32_t) * nlg * (size_t)s->ntot},
+            {S.snap_off, vsz * nlg * (size_t)s->ntot},
+            {S.hist, sizeof(int32_t) * nhist},
+            {S.ovf, sizeof(unsigned long long) * (size_t)s->nrep * nlg * s->n_dx},
+            {S.mom, sizeof(double) * (ns / 32) * nlg * 2}};
+}
+
+int md_checkpoint_bytes(md_system *s, int64_t *bytes) {
+    if (!s || !bytes) return fail(MD_E_ARG, "md_checkpoint_bytes: NULL argument");
+    size_t b = sizeof(CkptHeader);
+    for (const CkptPart &p : ckpt_parts(s, 0, 0)) b += p.bytes;
+    *bytes = (int64_t)b;
+    return MD_OK;
+}
+
+int md_checkpoint_save(md_system *s, void *buf) {
+    if (!s || !buf) return fail(MD_E_ARG, "md_checkpoint_save: NULL argument");
+    int rc = ensure_sorted(s);
+    if (rc) return rc;
+    rc = sync_status(s);
+    if (rc) return rc;
+    Control c;
+    MD_CUDA_TRY(cudaMemcpy(&c, s->d_ctl, sizeof(Control), cudaMemcpyDeviceToHost));
+    CkptHeader h{};
+    h.magic = CKPT_MAGIC;
+    h.version = 1;
+    h.step = s->step;
+    h.ntot = s->ntot;
+    h.n_rebuilds = c.n_rebuilds;
+    h.prec = s->prec;
+    h.nrep = s->nrep;
+    h.nslots = s->nslots;
+    h.n_lg = s->n_lg;
+    h.n_dx = s->n_dx;
+    h.nb = s->nb;
+    h.phase_half = s->phase_half;
+    unsigned char *o = static_cast<unsigned char *>(buf);
+    std::memcpy(o, &h, sizeof(h));
+    o += sizeof(h);
+    for (const CkptPart &p : ckpt_parts(s, c.set, c.cur)) {
+        MD_CUDA_TRY(cudaMemcpy(o, p.dev, p.bytes, cudaMemcpyDeviceToHost));
+        o += p.bytes;
+    }
+    return MD_OK;
+}
+
+int md_checkpoint_load(md_system *s, const void *buf) {
+    if (!s || !buf) return fail(MD_E_ARG, "md_checkpoint_load: NULL argument");
+    CkptHeader h;
+    std::memcpy(&h, buf, sizeof(h));
+    if (h.magic != CKPT_MAGIC || h.version != 1) return fail(MD_E_ARG, "md_checkpoint_load: not a checkpoint");
+    if (h.ntot != s->ntot || h.prec != s->prec || h.nrep != s->nrep || h.nslots != s->nslots ||
+        h.n_lg != s->n_lg || h.n_dx != s->n_dx || h.nb != s->nb)
+        return fail(MD_E_ARG, "md_checkpoint_load: the checkpoint was made by a system of other parameters");
+    int rc = sync_status(s);
+    if (rc) return rc;
+    // the state goes to set 0, buffer 0; then a sort that moves no particle
+    MD_CUDA_TRY(cudaMemset(&s->d_ctl->set, 0, 2 * sizeof(int)));
+    const unsigned char *o = static_cast<const unsigned char *>(buf) + sizeof(h);
+    for (const CkptPart &p : ckpt_parts(s, 0, 0)) {
+        MD_CUDA_TRY(cudaMemcpy(p.dev, o, p.bytes, cudaMemcpyHostToDevice));
+        o += p.bytes;
+    }
+    MD_CUDA_TRY(cudaMemcpy(&s->d_ctl->n_rebuilds, &h.n_rebuilds, sizeof(long long), cudaMemcpyHostToDevice));
+    MD_CUDA_TRY(cudaMemset(s->d_ctl->vmax, 0, sizeof(s->d_ctl->vmax)));
+    MD_CUDA_TRY(cudaMemset(s->sd.vmax_rep, 0, sizeof(unsigned) * 3 * (size_t)s->nrep));
+    s->step = h.step;
+    s->phase_half = h.phase_half;
+    s->needs_sort = true;
+    rc = ensure_sorted(s);
+    if (rc) return rc;
+    return sync_status(s);
+}
+
 int md_barrier_selftest(md_system *s, double limit_s) {
     if (!s || !(limit_s > 0.0) || !(limit_s <= 4.0)) return fail(MD_E_ARG, "md_barrier_selftest: bad arguments");
     if (s->grid < 2) return fail(MD_E_ARG, "md_barrier_selftest: needs a launch of at least 2 CTAs");
@@ -1392,6 +1578,56 @@ int feq_measured(md_system *s, int32_t rep, int32_t lg, int32_t dxi, int32_t sym
         stats->n_samples = (int64_t)R.n * A.nwin;
         stats->n_blocks_used = used;
     }
+    return MD_OK;
+}
+
+int md_hist_blocks(md_system *s, int32_t rep, int32_t lg, int32_t dxi, int32_t *hist, int64_t *wblk) {
+    if (!s || !hist || !wblk || rep < 0 || rep >= s->nrep || lg < 0 || lg >= s->n_lg || dxi < 0 ||
+        dxi >= s->n_dx)
+        return fail(MD_E_ARG, "md_hist_blocks: bad arguments");
+    const size_t base = ((size_t)(rep * s->n_lg + lg) * s->n_dx + dxi);
+    MD_CUDA_TRY(cudaMemcpyAsync(hist, s->sd.hist + base * MD_NBLK * s->nb, sizeof(int32_t) * MD_NBLK * s->nb,
+                                cudaMemcpyDeviceToHost, s->st));
+    int rc = sync_status(s);
+    if (rc) return rc;
+    for (int b = 0; b < MD_NBLK; ++b) wblk[b] = 0;
+    for (long long w = 0; w < windows_done(s, lg); ++w) wblk[(w / s->block_windows) % MD_NBLK] += 1;
+    return MD_OK;
+}
+
+int feq_bootstrap(md_system *s, int32_t lg, int32_t dxi, int32_t symmetrize, int32_t n_resamples, uint64_t seed,
+                  double *sigma_out) {
+    if (!s || !sigma_out || lg < 0 || lg >= s->n_lg || dxi < 0 || dxi >= s->n_dx || n_resamples < 2 ||
+        n_resamples > (1 << 20))
+        return fail(MD_E_ARG, "feq_bootstrap: bad arguments");
+    BootArgs A{};
+    A.reps = s->d_reps;
+    A.hist = s->sd.hist;
+    A.n_lg = s->n_lg;
+    A.n_dx = s->n_dx;
+    A.lg = lg;
+    A.dxi = dxi;
+    A.nb = s->nb;
+    A.W = s->W;
+    A.sym = symmetrize != 0;
+    A.B = n_resamples;
+    A.seed = seed;
+    for (long long w = 0; w < windows_done(s, lg); ++w) A.wblk[(w / s->block_windows) % MD_NBLK] += 1;
+    const size_t bytes = sizeof(double) * (size_t)s->nrep * s->nb;
+    cudaPointerAttributes at{};
+    const bool dev = cudaPointerGetAttributes(&at, sigma_out) == cudaSuccess && at.type == cudaMemoryTypeDevice;
+    cudaGetLastError();
+    double *dst = sigma_out;
+    if (!dev) MD_CUDA_TRY(cudaMallocAsync((void **)&dst, bytes, s->st));
+    A.sigma = dst;
+    k_feq_bootstrap<<<s->nrep, 128, 0, s->st>>>(A);
+    cudaError_t e = cudaGetLastError();
+    if (!dev) {
+        if (e == cudaSuccess) e = cudaMemcpyAsync(sigma_out, dst, bytes, cudaMemcpyDeviceToHost, s->st);
+        cudaFreeAsync(dst, s->st);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s->st);
+    }
+    if (e != cudaSuccess) return fail(MD_E_CUDA, "feq_bootstrap: %s", cudaGetErrorString(e));
     return MD_OK;
 }
 

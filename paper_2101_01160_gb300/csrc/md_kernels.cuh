@@ -969,8 +969,10 @@ __global__ void __launch_bounds__(BLOCK, md_min_ctas(BLOCK, DENSE)) k_md_persist
         __syncthreads();   // s_due / s_win / s_vmax are rewritten in the next step
     }
     if (blockIdx.x == 0) {
-        // every replica's bound is the batch's
-        for (int r = tid; r < S.nrep; r += BLOCK) S.disp_rep[r] = disp;
+        // every replica's bound is the batch's (a sort that moved nothing
+        // keeps the replicas' own bounds)
+        if (nsteps > 0 || force_rebuild == RB_ALL)
+            for (int r = tid; r < S.nrep; r += BLOCK) S.disp_rep[r] = disp;
         if (tid == 0) {
             C->set = set;
             C->cur = cur;

@@ -85,10 +85,15 @@ _SIGS = {
     "md_forces": ([P, P, P, P], C.c_int),
     "md_step_forces": ([P, C.c_int64, P, P], C.c_int),
     "md_energy": ([P, C.c_int32, P], C.c_int),
+    "md_checkpoint_bytes": ([P, C.POINTER(C.c_int64)], C.c_int),
+    "md_checkpoint_save": ([P, P], C.c_int),
+    "md_checkpoint_load": ([P, P], C.c_int),
     "md_hist_raw": ([P, C.c_int32, C.c_int32, C.c_int32, P, P, P], C.c_int),
     "feq_measured": ([P, C.c_int32, C.c_int32, C.c_int32, C.c_int32, P, P,
                       C.POINTER(md_feq_stats)], C.c_int),
     "feq_batch": ([P, C.c_int32, C.c_int32, C.c_int32, P], C.c_int),
+    "md_hist_blocks": ([P, C.c_int32, C.c_int32, C.c_int32, P, P], C.c_int),
+    "feq_bootstrap": ([P, C.c_int32, C.c_int32, C.c_int32, C.c_int32, C.c_uint64, P], C.c_int),
     "mdlg_bin": ([C.POINTER(md_snapshot), C.POINTER(md_snapshot), C.c_int64, C.c_int32, C.c_int32,
                   P, P, P, P], C.c_int),
     "mdlg_bin_noalloc": ([C.POINTER(md_snapshot), C.POINTER(md_snapshot), C.c_int64, C.c_int32,
@@ -276,6 +281,19 @@ class System:
         _check(load().md_step_forces(self.h, int(nsteps), _ptr(fx), _ptr(fy)))
         return fx, fy
 
+    def checkpoint(self):
+        """Exact checkpoint (md_checkpoint_save) as a host byte array."""
+        n = C.c_int64()
+        _check(load().md_checkpoint_bytes(self.h, C.byref(n)))
+        buf = np.empty(n.value, np.uint8)
+        _check(load().md_checkpoint_save(self.h, _ptr(buf)))
+        return buf
+
+    def restore(self, buf):
+        """Restores a checkpoint of a system with the same parameters."""
+        buf = np.ascontiguousarray(buf, dtype=np.uint8)
+        _check(load().md_checkpoint_load(self.h, _ptr(buf)))
+
     def energy(self, rep=0):
         out = np.zeros(4)
         _check(load().md_energy(self.h, rep, _ptr(out)))
@@ -328,6 +346,23 @@ def feq_batch(system, lg=0, dxi=0, symmetrize=True, out=None):
     buf = np.zeros((nrep, stride))
     _check(load().feq_batch(system.h, lg, dxi, int(symmetrize), _ptr(buf)))
     return buf[:, :nb], buf[:, nb:2 * nb], buf[:, 2 * nb:3 * nb], buf[:, 3 * nb:]
+
+
+def hist_blocks(system, rep=0, lg=0, dxi=0):
+    """Integer histogram per error-bar block: (int32 [MD_NBLK, nb], int64
+    windows per block [MD_NBLK])."""
+    h = np.zeros((MD_NBLK, system.nb), np.int32)
+    w = np.zeros(MD_NBLK, np.int64)
+    _check(load().md_hist_blocks(system.h, rep, lg, dxi, _ptr(h), _ptr(w)))
+    return h, w
+
+
+def feq_bootstrap(system, lg=0, dxi=0, symmetrize=False, n_resamples=200, seed=0):
+    """Block-bootstrap standard error of P_i for every replica: [n_rep, nb]."""
+    out = np.zeros((len(system.params), system.nb))
+    _check(load().feq_bootstrap(system.h, lg, dxi, int(symmetrize), int(n_resamples),
+                                C.c_uint64(seed & (2 ** 64 - 1)), _ptr(out)))
+    return out
 
 
 def _snapshots(cell0, ox0, oy0, cell1, ox1, oy1, ncell, h):
