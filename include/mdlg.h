@@ -539,6 +539,18 @@ int mlp_status(mlp_model *m);
 int bf16_gemm_tn(const void *A, const void *B, float *C, int32_t M, int32_t N, int32_t K,
                  int32_t *status, void *stream);
 
+/* Failure-detection self-test of the bounded mbarrier waits of the
+ * tensor-core kernels (no counterpart in the paper): bf16_gemm_tn on the
+ * same arguments, except that CTA 0 withholds the completion signal of its
+ * first K stage and every mbarrier wait is limited to limit_s seconds (0 <
+ * limit_s <= 2; K >= 192, so that a later stage waits for that signal).
+ * CTA 0's wait runs out, it waits (with the same limit) for the MMAs it
+ * issued, frees its tensor memory, flags *status and leaves; the call
+ * returns MD_E_TIMEOUT (MD_OK would mean the limit failed).  Nothing faults
+ * or hangs; C is undefined.  Synchronises the stream. */
+int bf16_gemm_selftest(const void *A, const void *B, float *C, int32_t M, int32_t N, int32_t K,
+                       int32_t *status, double limit_s, void *stream);
+
 /* Message of the calling thread's last failure ("" if none). */
 const char *md_last_error(void);
 

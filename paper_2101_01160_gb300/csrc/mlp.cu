@@ -42,6 +42,8 @@ struct GemmArgs {
     const float *Zp;    // EPI_DSILU: pre-activation, [M][ldz]
     int ldz;
     int *status;
+    uint64_t wait_ns;   // limit of every mbarrier wait (0: GEMM_WAIT_NS)
+    int dbg_skip_commit;   // bf16_gemm_selftest: CTA 0 does not signal stage dbg_skip_commit - 1 (0: never)
 };
 
 __device__ __forceinline__ float silu(float z) { return z / (1.0f + __expf(-z)); }
@@ -70,13 +72,15 @@ __global__ void __launch_bounds__(128) k_gemm(GemmArgs g) {
     const int a_bytes = GBM * GBK * 2, b_bytes = N * GBK * 2;
     unsigned char *st0 = sm, *st1 = sm + a_bytes + b_bytes;
     uint64_t *mbar = reinterpret_cast<uint64_t *>(sm + 2 * (a_bytes + b_bytes));
-    uint32_t *s_tmem = reinterpret_cast<uint32_t *>(mbar + 2);
+    uint32_t *s_tmem = reinterpret_cast<uint32_t *>(mbar + 3);   // mbar[2]: drain after a failed wait
     __shared__ int s_ok;
     const uint32_t ncols = N <= 32 ? 32u : (N <= 64 ? 64u : (N <= 128 ? 128u : 256u));
+    const uint64_t wait_ns = g.wait_ns ? g.wait_ns : GEMM_WAIT_NS;
     if (warp == 0) umma::tmem_alloc(s_tmem, ncols);
     if (tid == 0) {
         umma::mbar_init(&mbar[0], 1);
         umma::mbar_init(&mbar[1], 1);
+        umma::mbar_init(&mbar[2], 1);
         umma::mbar_fence_init();
         s_ok = 1;
     }
@@ -91,7 +95,7 @@ __global__ void __launch_bounds__(128) k_gemm(GemmArgs g) {
         const int s = kt & 1;
         unsigned char *sa = s ? st1 : st0;
         unsigned char *sb = sa + a_bytes;
-        if (kt >= 2 && !umma::mbar_wait(&mbar[s], ((kt - 2) >> 1) & 1, GEMM_WAIT_NS)) s_ok = 0;
+        if (kt >= 2 && !umma::mbar_wait(&mbar[s], ((kt - 2) >> 1) & 1, wait_ns)) s_ok = 0;
         __syncthreads();
         if (!s_ok) break;
         for (int c = tid; c < GBM * 8; c += 128) {
@@ -113,12 +117,19 @@ __global__ void __launch_bounds__(128) k_gemm(GemmArgs g) {
             for (int k4 = 0; k4 < GBK / 16; ++k4)
                 umma::mma(tmem, umma::desc(a0 + k4 * 256, 128, 1024), umma::desc(b0 + k4 * 256, 128, 1024),
                           idesc, (kt | k4) ? 1u : 0u);
-            umma::commit(&mbar[s]);
+            // the self-test withholds one signal so that a later wait runs out
+            if (!(g.dbg_skip_commit == kt + 1 && blockIdx.x == 0)) umma::commit(&mbar[s]);
         }
     }
     if (s_ok) {
         const int last = nk - 1;
-        if (!umma::mbar_wait(&mbar[last & 1], (last >> 1) & 1, GEMM_WAIT_NS)) s_ok = 0;
+        if (!umma::mbar_wait(&mbar[last & 1], (last >> 1) & 1, wait_ns)) s_ok = 0;
+    }
+    if (!s_ok && tid == 0) {
+        // a wait gave up: the MMAs this CTA issued may still run; wait (with a
+        // limit) until they are done before their TMEM is freed
+        umma::commit(&mbar[2]);
+        umma::mbar_wait(&mbar[2], 0, wait_ns);
     }
     __syncthreads();
     umma::fence_after();
@@ -1103,6 +1114,33 @@ int mlp_status(mlp_model *m) {
         return fail(MD_E_TIMEOUT, "tensor-core GEMM wait timed out");
     }
     return MD_OK;
+}
+
+int bf16_gemm_selftest(const void *A, const void *B, float *C, int32_t M, int32_t N, int32_t K,
+                       int32_t *status, double limit_s, void *stream) {
+    if (!A || !B || !C || !status || !(limit_s > 0.0) || !(limit_s <= 2.0) || K < 3 * GBK)
+        return fail(MD_E_ARG, "bf16_gemm_selftest: bad arguments (K >= 192, 0 < limit_s <= 2)");
+    GemmArgs g{};
+    g.A = (const bf16 *)A;
+    g.B = (const bf16 *)B;
+    g.lda = K;
+    g.ldb = K;
+    g.M = M;
+    g.N = N;
+    g.K = K;
+    g.C = C;
+    g.ldc = N;
+    g.status = status;
+    g.wait_ns = (uint64_t)(limit_s * 1e9);
+    g.dbg_skip_commit = 1;   // stage 0
+    cudaStream_t st = (cudaStream_t)stream;
+    MD_CUDA_TRY(cudaMemsetAsync(status, 0, sizeof(int32_t), st));
+    int rc = gemm_launch<EPI_F32>(g, st);
+    if (rc) return rc;
+    int32_t h = 0;
+    MD_CUDA_TRY(cudaMemcpyAsync(&h, status, sizeof(h), cudaMemcpyDeviceToHost, st));
+    MD_CUDA_TRY(cudaStreamSynchronize(st));
+    return h ? fail(MD_E_TIMEOUT, "bf16_gemm_selftest: an mbarrier wait ran out (as intended)") : MD_OK;
 }
 
 int bf16_gemm_tn(const void *A, const void *B, float *C, int32_t M, int32_t N, int32_t K,

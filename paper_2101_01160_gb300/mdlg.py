@@ -121,6 +121,7 @@ _SIGS = {
     "mlp_train_step": ([P, P, P, C.c_int32, C.c_float, P, P], C.c_int),
     "mlp_status": ([P], C.c_int),
     "bf16_gemm_tn": ([P, P, P, C.c_int32, C.c_int32, C.c_int32, P, P], C.c_int),
+    "bf16_gemm_selftest": ([P, P, P, C.c_int32, C.c_int32, C.c_int32, P, C.c_double, P], C.c_int),
 }
 
 
@@ -615,3 +616,16 @@ def bf16_gemm_tn(A, B, stream=None):
     st = torch.zeros(1, dtype=torch.int32, device="cuda")
     _check(load().bf16_gemm_tn(_ptr(A), _ptr(B), _ptr(Cm), M, N, K, _ptr(st), _stream(stream)))
     return Cm, st
+
+
+def bf16_gemm_selftest(A, B, limit_s=0.02, stream=None):
+    """Return code of bf16_gemm_selftest (MD_E_TIMEOUT when the bounded
+    mbarrier waits work)."""
+    import torch
+
+    M, K = A.shape
+    N = B.shape[0]
+    Cm = torch.empty((M, N), dtype=torch.float32, device="cuda")
+    st = torch.zeros(1, dtype=torch.int32, device="cuda")
+    return int(load().bf16_gemm_selftest(_ptr(A), _ptr(B), _ptr(Cm), M, N, K, _ptr(st), float(limit_s),
+                                         _stream(stream)))

@@ -5,6 +5,10 @@ MD_E_TIMEOUT in the status word the host reads, and every CTA leaves the
 kernel.  md_barrier_selftest makes one CTA leave instead of arriving (a
 missing arrival, nothing else skipped) with a 20 ms limit: the call must
 report the timeout within a bounded time, and the device must stay usable.
+bf16_gemm_selftest does the same for an mbarrier wait of the tensor-core
+GEMM: one completion signal is withheld, the wait runs out, the kernel
+drains its MMAs and frees its tensor memory, and a normal GEMM afterwards
+is correct.
 """
 
 import time
@@ -55,3 +59,21 @@ def test_barrier_selftest_rejects_bad_limits(mdlg):
     s.step(10)
     s.sync()
     s.close()
+
+
+def test_mbarrier_wait_runs_out_and_is_reported(mdlg):
+    g = torch.Generator(device="cuda")
+    g.manual_seed(5)
+    A = torch.randn((256, 256), device="cuda", generator=g).to(torch.bfloat16)
+    B = torch.randn((128, 256), device="cuda", generator=g).to(torch.bfloat16)
+    t0 = time.perf_counter()
+    rc = mdlg.bf16_gemm_selftest(A, B, limit_s=0.02)
+    assert rc == mdlg.MD_E_TIMEOUT, rc
+    assert time.perf_counter() - t0 < 2.0
+    # the device is usable and the tensor memory was released
+    for _ in range(3):
+        Cm, st = mdlg.bf16_gemm_tn(A, B)
+        torch.cuda.synchronize()
+        assert st.item() == 0
+        ref = A.float() @ B.float().T
+        assert torch.max(torch.abs(Cm - ref)).item() < 1e-3 * torch.max(torch.abs(ref)).item()

@@ -102,17 +102,54 @@ def test_training_lowers_loss(mdlg, orc):
 
 def test_surrogate_pipeline_beats_md_free_baseline(mdlg):
     """End to end on a reduced ensemble: MD-measured equilibria as training
-    data, tensor-core training, held-out replicas; the surrogate (no MD at
-    query time) must beat the ballistic Gaussian (the other MD-free
-    prediction) and stay within 2e-2 of every measured class."""
+    data, tensor-core training, held-out replicas run 5x longer (their
+    labels' sampling error is small against the bar); the surrogate (no MD
+    at query time) must beat the ballistic Gaussian (the other MD-free
+    prediction) and stay within 1.5e-2 of every measured class (measured
+    9.1e-3 with this small set and short training; the full pipeline of
+    surrogate.main reaches 1.3e-3)."""
     from paper_2101_01160_gb300 import surrogate
 
-    ds = surrogate.generate(31, n_rep=96, steps=8000, n_equil=2000, n_min=2048, n_max=8192)
-    tr, te = surrogate.split(ds, 0.15, seed=1)
-    assert len(tr.X) > 300 and len(te.X) > 30
+    tr = surrogate.generate(31, n_rep=96, steps=8000, n_equil=2000, n_min=2048, n_max=8192)
+    te = surrogate.generate(32, n_rep=24, steps=40_000, n_equil=2000, n_min=2048, n_max=8192,
+                            rep_offset=5000)
+    assert len(tr.X) > 300 and len(te.X) > 60
     m = surrogate.new_model(3)
-    hist = surrogate.train(m, tr, steps=3000, batch=512, log_every=500)
+    hist = surrogate.train(m, tr, steps=6000, lr=1e-3, batch=512, log_every=1000)
     assert hist[-1][1] < 0.3 * hist[0][1], hist
     res = surrogate.evaluate(m, te)
+    print(res)
     assert res["surrogate"]["median"] < res["gauss_ballistic"]["median"], res
-    assert res["surrogate"]["max"] < 2e-2, res
+    assert res["surrogate"]["max"] < 1.5e-2, res
+
+
+def test_predictor_falls_back_to_wsg(mdlg):
+    """Outside the training box, or where the two networks disagree beyond
+    the tolerance, the prediction is the WSG equilibrium at the supplied
+    moments (Eqs. f_eq_wsg, lambda_eq); inside, the networks' mean."""
+    import torch
+
+    from paper_2101_01160_gb300 import surrogate
+
+    ms = [surrogate.new_model(s) for s in (5, 6)]
+    lo, hi = np.array([0.02, 1.0, 0.05, 1.0]), np.array([0.30, 20.0, 0.2, 4.0])
+    X = np.array([[0.1, 10.0, 0.1, 2.0],      # inside
+                  [0.5, 10.0, 0.1, 2.0],      # phi outside
+                  [0.1, 30.0, 0.1, 2.0]], np.float32)
+    mom = np.array([[0.05, 0.05 ** 2 * 3.3, 1.0], [0.3, 0.3 ** 2 * 3.2, 2.0], [0.9, 0.9 ** 2 * 3.1, 2.0]])
+    pred = surrogate.Predictor(ms, lo, hi, tol=1.0)      # no disagreement limit
+    P, fb, spread = pred(X, mom)
+    assert list(fb) == [False, True, True]
+    mean = np.mean([m.forward(torch.from_numpy(X).cuda()).cpu().numpy() for m in ms], axis=0)
+    assert np.allclose(P[0], mean[0], rtol=0, atol=1e-7)
+    for i in (1, 2):
+        mu2, mu4, dx = mom[i]
+        lam, _ = mdlg.wsg_lambda(mu2, mu4, allow_domain=True)
+        ref = mdlg.feq_wsg(mu2 / dx ** 2, lam.item(), W=4).cpu().numpy()
+        assert np.array_equal(P[i], ref)
+    # untrained networks of different seeds disagree: a tight limit sends
+    # every query to the fallback
+    P2, fb2, sp2 = surrogate.Predictor(ms, lo, hi, tol=1e-6)(X, mom)
+    assert fb2.all() and np.all(sp2 > 1e-6)
+    with pytest.raises(ValueError):
+        pred(X)
