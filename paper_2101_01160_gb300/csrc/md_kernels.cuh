@@ -62,6 +62,7 @@ struct Control {
     long long n_rebuilds;
     unsigned vmax[3];     // global engine: per-step max |v| dt / half_skin (float bits), by step mod 3
     unsigned pad1;
+    unsigned long long claims;   // global engine: chunk claims of this launch (zeroed before it)
 };
 
 // Everything the kernels need, passed by value.
@@ -71,6 +72,7 @@ struct SysDev {
     const int4 *chunks;         // {rep, first slot, end slot, 0}
     Control *ctl;
     int32_t nslots, nrep, total_cells, nchunks, ppt, K, stage;
+    int32_t nstatic;            // chunks [0, nstatic) dealt to CTAs, the rest claimed
     int32_t n_lg, n_dx, W, nb, block_windows;
     long long n_equil;
     int32_t lg_every[MD_MAX_LG];
@@ -329,6 +331,93 @@ __device__ __forceinline__ int own_chunks(int nchunks) {
 }
 __device__ __forceinline__ int own_chunk(int i) { return (int)blockIdx.x + i * (int)gridDim.x; }
 
+// Work distribution of the global-memory shapes: runs body(cd, g0) for every
+// 32-slot group of every chunk of one pass, each on exactly one warp (cd the
+// chunk, g0 its group's first slot; lanes past the chunk's end have
+// slot >= cd.z).  Chunks [0, nstatic) are dealt to CTAs (own_chunk), their
+// groups to the CTA's warps in turn.  The rest, the cheapest, are claimed:
+// a CTA claims whole chunks from the launch's counter (zeroed before the
+// launch) in table order and holds one claimed chunk in reserve; its warps
+// take the groups of its current chunk from a shared-memory counter, with no
+// CTA-wide sync, so that all CTAs finish the pass within about one group of
+// each other.  The warp that takes the group just past the end installs the
+// reserve (the first such warp of the pass claims it first) and claims the
+// next; warps that overshot wait for the install (shared memory, bounded:
+// DS_TIMEOUT after about 2^22 polls).  Every CTA stops claiming at its first
+// claim past the table, so a pass issues exactly (nchunks - nstatic) +
+// gridDim.x claims and every CTA advances base to the next pass's first value
+// without reading the counter; grid barriers separate passes.  Which warp
+// computes a group changes no result.
+constexpr int GRP_BITS = 10;   // group field of the shared work word
+template <int BLOCK, typename F>
+__device__ __forceinline__ void for_each_group(const SysDev &S, unsigned long long &base, F &&body) {
+    // s_work = (current chunk - nstatic + 1) << GRP_BITS | next group; 0 in
+    // the chunk field before the first install, ndyn + 1 once none is left
+    __shared__ unsigned s_work;
+    __shared__ int s_pend;   // reserve chunk; -1 while its claim is in flight, -2 none yet
+    const int nch = S.nchunks, nst = S.nstatic, lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int ndyn = nch - nst;
+    const auto claim = [&]() {
+        const unsigned long long v = atomicAdd(&S.ctl->claims, 1ull) - base;
+        return v < (unsigned long long)ndyn ? nst + (int)v : nch;
+    };
+    __syncthreads();   // the previous pass's readers of s_work / s_pend are done
+    if (threadIdx.x == 0) {
+        s_work = 0u;
+        s_pend = -2;
+    }
+    __syncthreads();
+    const int ndealt = own_chunks(nst);
+    for (int i = 0; i < ndealt; ++i) {
+        const int4 cd = S.chunks[own_chunk(i)];
+        const int ng = (cd.z - cd.y + 31) >> 5;
+        for (int g = warp; g < ng; g += BLOCK / 32) body(cd, cd.y + 32 * g);
+    }
+    if (ndyn <= 0) return;
+    for (;;) {
+        unsigned w = 0;
+        if (lane == 0) w = atomicAdd(&s_work, 1u);
+        w = __shfl_sync(0xffffffffu, w, 0);
+        const int cf = (int)(w >> GRP_BITS), g = (int)(w & ((1u << GRP_BITS) - 1));
+        const int c = nst + cf - 1;   // nst - 1: none installed yet
+        if (c >= nch) break;
+        int4 cd = make_int4(0, 0, 0, 0);
+        if (cf > 0) cd = S.chunks[c];
+        const int ng = (cd.z - cd.y + 31) >> 5;   // 0 before the first install
+        if (g < ng) {
+            body(cd, cd.y + 32 * g);
+            continue;
+        }
+        int ok = 1;
+        if (lane == 0) {
+            unsigned polls = 0;
+            if (g == ng) {
+                // install the reserve once its claim has landed, then claim anew
+                int nc;
+                while ((nc = *(volatile int *)&s_pend) == -1 && ++polls < (1u << 22)) __nanosleep(32);
+                if (nc == -2) nc = claim();
+                if (nc >= 0) {
+                    *(volatile int *)&s_pend = -1;
+                    __threadfence_block();
+                    atomicExch(&s_work, (unsigned)(nc - nst + 1) << GRP_BITS);
+                    const int nxt = nc < nch ? claim() : nch;
+                    *(volatile int *)&s_pend = nxt;
+                } else {
+                    ok = 0;
+                }
+            } else {
+                // another warp installs the next chunk
+                while ((int)(*(volatile unsigned *)&s_work >> GRP_BITS) == cf && ++polls < (1u << 22))
+                    __nanosleep(32);
+                ok = polls < (1u << 22);
+            }
+            if (!ok) atomicOr(&S.ctl->status, (int)DS_TIMEOUT);
+        }
+        if (!__shfl_sync(0xffffffffu, ok, 0)) break;
+    }
+    base += (unsigned long long)ndyn + gridDim.x;
+}
+
 
 // ---------------------------------------------------------------- neighbour lists
 // Builds the list of slot i from the 3x3 cell stencil (same row/cell order
@@ -443,7 +532,7 @@ enum RebuildMode { RB_ALL = 1, RB_NONE = 2 };
 
 template <typename T, int BLOCK>
 __device__ bool rebuild(const SysDev &S, int &set, int &cur, unsigned &gen, int nloc,
-                        ChunkDesc *s_desc, int mode) {
+                        ChunkDesc *s_desc, int mode, unsigned long long &claim0) {
     using V = typename V2<T>::type;
     Control *C = S.ctl;
     const GridBarrier bar{&C->bar_count, &C->bar_gen, &C->status};
@@ -588,27 +677,36 @@ __device__ bool rebuild(const SysDev &S, int &set, int &cur, unsigned &gen, int 
     if (!grid_sync(bar, gen, S.timeout_ns)) return false;
     set ^= 1;
     cur = 0;
-    // R7: chunk windows and neighbour lists of the CTA's own slots (read only
-    // by this CTA, so no barrier follows)
+    // R7: neighbour lists.  Staged shapes: the chunk windows and lists of
+    // the CTA's own chunks, read only by this CTA, so no barrier follows.
+    // Global-memory shapes: lists of groups taken from the dynamic
+    // distribution, which any warp may read next, so a barrier follows.
     {
         const V *npos = static_cast<const V *>(S.pos[set][0]);
         const uint32_t *ncell = S.cell[set];
-        for (int i = tid; i < nloc; i += BLOCK)
-            s_desc[i] = make_desc(S, ncell, own_chunk(i), WinParts<T>::value);
-        __syncthreads();
         int over = 0;
-        for (int i = 0; i < nloc; ++i) {
-            const ChunkDesc d = s_desc[i];
-            const RepDev &R = S.reps[d.rep];
-            for (int slot = d.start + tid; slot < d.end; slot += BLOCK) {
-                const int cnt = build_list<T>(S, R, npos, ncell[slot], npos[slot], slot);
-                S.nn[slot] = cnt < S.K ? cnt : S.K;
-                over |= cnt > S.K;
-            }
+        const auto list_of = [&](int slot, const RepDev &R) {
+            const int cnt = build_list<T>(S, R, npos, ncell[slot], npos[slot], slot);
+            S.nn[slot] = cnt < S.K ? cnt : S.K;
+            over |= cnt > S.K;
+        };
+        if (S.stage) {
+            for (int i = tid; i < nloc; i += BLOCK)
+                s_desc[i] = make_desc(S, ncell, own_chunk(i), WinParts<T>::value);
+            __syncthreads();
+            for (int i = 0; i < nloc; ++i)
+                for (int slot = s_desc[i].start + tid; slot < s_desc[i].end; slot += BLOCK)
+                    list_of(slot, S.reps[s_desc[i].rep]);
+        } else {
+            for_each_group<BLOCK>(S, claim0, [&](const int4 &cd, int g0) {
+                const int slot = g0 + (tid & 31);
+                if (slot < cd.z) list_of(slot, S.reps[cd.x]);
+            });
         }
         if (__syncthreads_or(over) && tid == 0) atomicOr(&C->status, (int)DS_NBR_OVERFLOW);
     }
     if (blockIdx.x == 0 && tid == 0) C->n_rebuilds += 1;
+    if (!S.stage && !grid_sync(bar, gen, S.timeout_ns)) return false;
     return true;
 }
 
@@ -795,6 +893,7 @@ __global__ void __launch_bounds__(BLOCK, md_min_ctas(BLOCK, DENSE)) k_md_persist
     if (tid == 0) gen = ld_acquire_gpu(&C->bar_gen);
     int set = C->set, cur = C->cur;
     const int nloc = own_chunks(S.nchunks);
+    unsigned long long claim0 = 0;   // claim counter at the start of the next claiming pass
     const int per_lg = S.n_dx * S.nb;
     for (int e = tid; e < S.n_lg * per_lg; e += BLOCK) sh_hist[e] = 0;
     // one bound for the whole batch: the largest of the replicas' bounds (a
@@ -812,7 +911,7 @@ __global__ void __launch_bounds__(BLOCK, md_min_ctas(BLOCK, DENSE)) k_md_persist
     if (force_rebuild) {
         // RB_ALL: canonical cells (a new state); RB_NONE: sort and lists of a
         // state written in another order, no particle's cell moved
-        if (!rebuild<T, BLOCK>(S, set, cur, gen, nloc, s_desc, force_rebuild)) return;
+        if (!rebuild<T, BLOCK>(S, set, cur, gen, nloc, s_desc, force_rebuild, claim0)) return;
         if (force_rebuild == RB_ALL) disp = 0.0;
     } else {
         for (int i = tid; i < nloc; i += BLOCK)
@@ -874,22 +973,22 @@ __global__ void __launch_bounds__(BLOCK, md_min_ctas(BLOCK, DENSE)) k_md_persist
             }
             cp_async_wait<0>();
         } else {
-            // neighbours straight from global memory (L1/L2); no CTA-wide sync
-            ChunkDesc none{};
-            for (int i = 0; i < nloc; ++i) {
-                const int4 cd = S.chunks[own_chunk(i)];
+            // neighbours straight from global memory (L1/L2); groups from the
+            // dynamic distribution (for_each_group)
+            const ChunkDesc none{};
+            for_each_group<BLOCK>(S, claim0, [&](const int4 &cd, int g0) {
+                const int slot = g0 + lane;
+                if (slot >= cd.z) return;
                 const RepDev &R = S.reps[cd.x];
                 const T hk = rd<T>(R.hk, R.hkf), dt = rd<T>(R.dt, R.dtf);
                 const float vscale = (float)(R.dt / R.half_skin);
-                for (int slot = cd.y + tid; slot < cd.z; slot += BLOCK) {
-                    const V oi = pin[slot];
-                    const V vi = vel[slot];   // requested now, used after the force sum
-                    T fx = T(0), fy = T(0);
-                    lj_list<T>(S, R, none, nullptr, nullptr, pin, oi, slot, S.nn[slot], fx, fy);
-                    if (S.dbg_fx && it == nsteps - 1) debug_force(S, set, slot, fx, fy);
-                    kick_drift<T>(R, oi, vi, fx, fy, hk, dt, first, vscale, pout, vel, slot, vm, bad);
-                }
-            }
+                const V oi = pin[slot];
+                const V vi = vel[slot];   // requested now, used after the force sum
+                T fx = T(0), fy = T(0);
+                lj_list<T>(S, R, none, nullptr, nullptr, pin, oi, slot, S.nn[slot], fx, fy);
+                if (S.dbg_fx && it == nsteps - 1) debug_force(S, set, slot, fx, fy);
+                kick_drift<T>(R, oi, vi, fx, fy, hk, dt, first, vscale, pout, vel, slot, vm, bad);
+            });
         }
         for (int o = 16; o > 0; o >>= 1) vm = fmaxf(vm, __shfl_xor_sync(0xffffffffu, vm, o));
         if (lane == 0) s_vmax[tid >> 5] = vm;
@@ -963,7 +1062,7 @@ __global__ void __launch_bounds__(BLOCK, md_min_ctas(BLOCK, DENSE)) k_md_persist
             }
         }
         if (disp >= 1.0) {
-            if (!rebuild<T, BLOCK>(S, set, cur, gen, nloc, s_desc, RB_ALL)) return;
+            if (!rebuild<T, BLOCK>(S, set, cur, gen, nloc, s_desc, RB_ALL, claim0)) return;
             disp = 0.0;
         }
         __syncthreads();   // s_due / s_win / s_vmax are rewritten in the next step

@@ -120,6 +120,34 @@ def test_fused_sampling_uneven_batch_bench_shape(mdlg, orc):
     s.close()
 
 
+def test_dynamic_tail_bit_identical_to_dealt_chunks(mdlg):
+    """Global-memory launch shapes deal the first rounds of chunks to CTAs
+    and let CTAs claim the rest each step; a claimed chunk's neighbour list
+    was built by another CTA in the last rebuild.  Over many rebuilds of an
+    uneven batch large enough to have a claimed tail (about 30k particles
+    per replica, 48 replicas, so more than two rounds of chunks), the state,
+    histograms and rebuild count equal those of the staged shape, which
+    claims nothing."""
+    params, cat = _uneven_batch(mdlg, R=48, seed=23)
+    out = []
+    for shape in ((256, 1, 1), (256, 1, 3), (128, 1, 2)):
+        s = mdlg.System(params, *cat)
+        s.tune(*shape)
+        for _ in range(3):
+            s.step(300)
+        s.sync()
+        out.append((s.get_state(), [s.hist_raw(r, 0, 0)[0] for r in range(0, len(params), 5)],
+                    s.info().n_rebuilds))
+        s.close()
+    assert out[0][2] >= 20, out[0][2]
+    for o in out[1:]:
+        for u, v in zip(out[0][0], o[0]):
+            assert np.array_equal(u, v)
+        for u, v in zip(out[0][1], o[1]):
+            assert np.array_equal(u, v)
+        assert o[2] == out[0][2]
+
+
 @pytest.mark.parametrize("prec", [0, 1])
 def test_energy_matches_oracle(mdlg, orc, prec):
     """md_energy of each replica equals the oracle's kinetic energy, shifted
