@@ -1110,7 +1110,11 @@ __global__ void k_observe(SysDev S, ObsArgs A) {
             V v = vel[slot];
             T fx = T(0), fy = T(0);
             double fa = 0.0;
-            lj_stencil<T, true>(R, pos, S.cell_start, cpk, oi, slot, fx, fy, pe, fa);
+            // forces only for the outputs that use them (the half kick, the
+            // force readout, the potential energy); a snapshot or state
+            // readout needs none
+            if (A.complete || A.fx || A.epart)
+                lj_stencil<T, true>(R, pos, S.cell_start, cpk, oi, slot, fx, fy, pe, fa);
             if (A.complete) {
                 const T hk = rd<T>(R.hk, R.hkf);
                 v.x = axpyT(v.x, hk, fx);
