@@ -388,9 +388,10 @@ __device__ __forceinline__ int act_off(int r, int k) {
 
 // silu(z) = z sigmoid(z) = h + h tanh(h), h = z / 2: one special-function
 // operation (tanh.approx, relative error about 2^-11, below the BF16 rounding
-// of the stored activation).
-__device__ __forceinline__ float silu_fast(float z) {
-    const float h = 0.5f * z;
+// of the stored activation) and one FMA.  The hidden layers' packed weights
+// and biases are scaled by 1/2 (exact: a power of two), so the accumulator
+// already holds h, bit for bit the half of the unscaled pre-activation.
+__device__ __forceinline__ float silu_of_half(float h) {
     float t;
     asm("tanh.approx.f32 %0, %1;" : "=f"(t) : "f"(h));
     return fmaf(h, t, h);
@@ -604,8 +605,8 @@ __global__ void __launch_bounds__(F_THREADS, 1) k_mlp_fused(FusedArgs a) {
                         uint32_t hv[8];
 #pragma unroll
                         for (int i = 0; i < 8; ++i)
-                            hv[i] = pack_bf16(silu_fast(__uint_as_float(v[cur][2 * i])),
-                                              silu_fast(__uint_as_float(v[cur][2 * i + 1])));
+                            hv[i] = pack_bf16(silu_of_half(__uint_as_float(v[cur][2 * i])),
+                                              silu_of_half(__uint_as_float(v[cur][2 * i + 1])));
                         *reinterpret_cast<uint4 *>(act + act_off(r, cb + 16 * g)) = make_uint4(hv[0], hv[1], hv[2], hv[3]);
                         *reinterpret_cast<uint4 *>(act + act_off(r, cb + 16 * g + 8)) = make_uint4(hv[4], hv[5], hv[6], hv[7]);
                         if (g < 7) umma::wait_ld(v[nxt]);
@@ -690,34 +691,39 @@ __device__ __forceinline__ float split_part(float v, int part) {
     return part == 0 ? hi : v - hi;
 }
 
+// The packing kernels below multiply a hidden layer's operands by sc = 1/2
+// (the output layer's by 1), which is exact for BF16 values: the fused
+// kernel's accumulator then holds half the pre-activation (silu_of_half).
+
 // Packs layer 1, W [256][4] and b [256] FP32, into the split K = 16 operand
 // (W_hi, W_hi, W_lo, b_hi, b_lo, 0, 0) in the shared-memory layout.
-__global__ void k_pack0(const float *W, const float *b, bf16 *out) {
+__global__ void k_pack0(const float *W, const float *b, float sc, bf16 *out) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= 256 * 16) return;
     const int n = i / 16, k = i % 16;
     float v = 0.f;
     if (k < 12) v = split_part(W[n * 4 + (k & 3)], k < 8 ? 0 : 1);
     else if (k < 14) v = split_part(b[n], k - 12);
-    out[(n >> 3) * (F_SBO_B0 / 2) + (k >> 3) * 64 + (n & 7) * 8 + (k & 7)] = __float2bfloat16_rn(v);
+    out[(n >> 3) * (F_SBO_B0 / 2) + (k >> 3) * 64 + (n & 7) * 8 + (k & 7)] = __float2bfloat16_rn(sc * v);
 }
 
 // Packs the bias b [N] into the K = 16 operand (b_hi, b_lo, 0, ...).
-__global__ void k_packb(const float *b, int N, bf16 *out) {
+__global__ void k_packb(const float *b, int N, float sc, bf16 *out) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= N * 16) return;
     const int n = i / 16, k = i % 16;
     const float v = k < 2 ? split_part(b[n], k) : 0.f;
-    out[(n >> 3) * (F_SBO_B0 / 2) + (k >> 3) * 64 + (n & 7) * 8 + (k & 7)] = __float2bfloat16_rn(v);
+    out[(n >> 3) * (F_SBO_B0 / 2) + (k >> 3) * 64 + (n & 7) * 8 + (k & 7)] = __float2bfloat16_rn(sc * v);
 }
 
 // Packs W [N][256] (BF16 row-major) into 64-feature chunks laid out exactly
 // as the fused kernel's shared-memory weight buffer.
-__global__ void k_pack(const bf16 *W, int N, bf16 *out) {
+__global__ void k_pack(const bf16 *W, int N, float sc, bf16 *out) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= N * 256) return;
     const int n = i / 256, k = i % 256, kc = k / FK, kk = k % FK;
-    out[(size_t)kc * N * FK + (n >> 3) * (F_SBO_B / 2) + (kk >> 3) * 64 + (n & 7) * 8 + (kk & 7)] = W[i];
+    out[(size_t)kc * N * FK + (n >> 3) * (F_SBO_B / 2) + (kk >> 3) * 64 + (n & 7) * 8 + (kk & 7)] =
+        __float2bfloat16_rn(sc * __bfloat162float(W[i]));
 }
 
 }  // namespace mdlg
@@ -1025,11 +1031,12 @@ int mlp_forward(mlp_model *m, const float *X, int64_t M, float *P_out, void *str
     if ((uintptr_t)X & 15) return fail(MD_E_ARG, "mlp_forward: X must be 16-byte aligned");
     cudaStream_t st = (cudaStream_t)stream;
     if (!m->packed) {
-        k_pack0<<<16, 256, 0, st>>>(m->W[0], m->b[0], m->Wp[0]);
+        k_pack0<<<16, 256, 0, st>>>(m->W[0], m->b[0], m->nl > 1 ? 0.5f : 1.0f, m->Wp[0]);
         for (int l = 1; l < m->nl; ++l) {
             const int n = m->outp[l] * 256;
-            k_pack<<<(n + 255) / 256, 256, 0, st>>>(m->Wh[l], m->outp[l], m->Wp[l]);
-            k_packb<<<(m->outp[l] * 16 + 255) / 256, 256, 0, st>>>(m->b[l], m->outp[l], m->Bp[l]);
+            const float sc = l < m->nl - 1 ? 0.5f : 1.0f;
+            k_pack<<<(n + 255) / 256, 256, 0, st>>>(m->Wh[l], m->outp[l], sc, m->Wp[l]);
+            k_packb<<<(m->outp[l] * 16 + 255) / 256, 256, 0, st>>>(m->b[l], m->outp[l], sc, m->Bp[l]);
         }
         MD_CUDA_TRY(cudaGetLastError());
         m->packed = true;
@@ -1048,12 +1055,9 @@ int mlp_forward(mlp_model *m, const float *X, int64_t M, float *P_out, void *str
     }
     a.p_aligned = ((uintptr_t)P_out & 15) == 0;
     a.status = m->status;
-    static int nsm = 0;
-    if (!nsm) {
-        int dev = 0;
-        cudaGetDevice(&dev);
-        cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-    }
+    int dev = 0, nsm = 0;   // the calling thread's current device
+    MD_CUDA_TRY(cudaGetDevice(&dev));
+    MD_CUDA_TRY(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
     MD_CUDA_TRY(cudaFuncSetAttribute(k_mlp_fused, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)FUSED_SMEM));
     const long long tiles = (M + 127) / 128;
     const int grid = (int)std::min<long long>(tiles, nsm);
