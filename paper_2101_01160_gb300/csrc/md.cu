@@ -549,6 +549,10 @@ struct md_system {
     // global engine's cell lists need a sort-only rebuild after its launches
     int engine = 0;                   // 0 = k_md_persistent, 1 = k_md_resident
     bool needs_sort = false;
+    // the neighbour lists' layout depends on the launch shape (staged: slot
+    // order; global: sorted within each chunk of the chunk table), so a new
+    // shape's first launch rebuilds them (sort only)
+    bool lists_valid = false;
     std::vector<void *> res_allocs;
     ResDev rd{};
     int res_grid = 0;
@@ -901,6 +905,7 @@ int configure_launch(md_system *s, int block, int ppt, int stage) {
     s->sd.stage = stage == 1;
     s->stage = stage;
     s->engine = 0;
+    s->lists_valid = false;   // chunk table and list layout change with the shape
     return MD_OK;
 }
 
@@ -917,11 +922,12 @@ int ensure_sorted(md_system *s) {
 
 int launch_persistent(md_system *s, long long nsteps, int force_rebuild) {
     if (force_rebuild != RB_ALL) {
-        int rc = ensure_sorted(s);
-        if (rc) return rc;
+        if (s->needs_sort || !s->lists_valid) force_rebuild = RB_NONE;
+        s->needs_sort = false;
     } else {
         s->needs_sort = false;
     }
+    s->lists_valid = true;
     const void *fn = persistent_fn(s->prec, s->block, s->stage);
     long long step0 = s->step;
     int phase = s->phase_half;
@@ -1143,6 +1149,7 @@ int md_init_batch(const md_params *p, int32_t n_rep, const double *x, const doub
     ALLOC(S.perm, sizeof(int32_t) * ns);
     ALLOC(S.nbr, sizeof(uint32_t) * ns * (size_t)s->K);
     ALLOC(S.nn, sizeof(int32_t) * (ns + 16));   // staged four at a time
+    ALLOC(S.cnt_id, sizeof(int32_t) * (size_t)s->ntot);
     s->chunk_cap = (long long)(ns / 128) + n_rep + 1;
     ALLOC(s->d_chunks, sizeof(int4) * s->chunk_cap);
     ALLOC(S.blocksum, sizeof(int32_t) * 4096);
@@ -1194,6 +1201,7 @@ int md_init_batch(const md_params *p, int32_t n_rep, const double *x, const doub
     tryc(cudaMemsetAsync(s->d_ctl, 0, sizeof(Control), s->st));
     tryc(cudaMemsetAsync(S.perm, 0xff, sizeof(int32_t) * ns, s->st));   // padding slots: -1
     tryc(cudaMemsetAsync(S.nn, 0, sizeof(int32_t) * (ns + 16), s->st));
+    tryc(cudaMemsetAsync(S.cnt_id, 0, sizeof(int32_t) * (size_t)s->ntot, s->st));
     tryc(cudaMemsetAsync(S.cellcnt, 0, sizeof(int32_t) * s->total_cells, s->st));
     tryc(cudaMemsetAsync(S.hist, 0, sizeof(int32_t) * nhist, s->st));
     tryc(cudaMemsetAsync(S.ovf, 0, sizeof(unsigned long long) * n_rep * nlg * s->n_dx, s->st));

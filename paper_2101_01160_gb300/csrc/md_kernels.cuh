@@ -84,7 +84,12 @@ struct SysDev {
     // cell list and rebuild scratch
     int32_t *cellcnt, *cell_start, *newcell, *rank, *perm, *blocksum;
     uint32_t *nbr;              // [nslots/32][K][32]
-    int32_t *nn;                // neighbours of each slot
+    // neighbours of each slot.  Staged shapes: nn[slot] = count, lists in
+    // slot order.  Global-memory shapes: the slots of every chunk are laid
+    // out in order of decreasing list batches (sorted position q), list q
+    // and nn[q] = count | (slot - chunk start) << 16 belong to that slot.
+    int32_t *nn;
+    int32_t *cnt_id;            // [ntot] by particle id: list length at the last rebuild
     // sampling
     uint32_t *snap_cell;        // [n_lg][ntot] by particle id
     void *snap_off;             // [n_lg][ntot] Vec2<T>
@@ -426,13 +431,13 @@ __device__ __forceinline__ void for_each_group(const SysDev &S, unsigned long lo
 template <typename T>
 __device__ __forceinline__ int build_list(const SysDev &S, const RepDev &R,
                                           const typename V2<T>::type *pos, uint32_t cpk,
-                                          typename V2<T>::type oi, int self) {
+                                          typename V2<T>::type oi, int self, int at) {
     const int nc = R.nc;
     const int cx = (int)(cpk & 0xffffu), cy = (int)(cpk >> 16);
     const T h = rd<T>(R.h, R.hf);
     const T rv2 = rd<T>(R.rv2, R.rv2f);
     const int32_t *csr = S.cell_start + R.cbase;
-    uint32_t *out = S.nbr + (long long)(self >> 5) * S.K * 32 + (self & 31);
+    uint32_t *out = S.nbr + (long long)(at >> 5) * S.K * 32 + (at & 31);   // list position
     int cnt = 0;
     for (int oy = -1; oy <= 1; ++oy) {
         const int row = wrap1(cy + oy, nc) * nc;
@@ -519,6 +524,109 @@ __device__ __forceinline__ void lj_list(const SysDev &S, const RepDev &R, const 
     lj_list_from<T>(S, R, d, spos, pin, oi, self, cnt, e, fx, fy);
 }
 
+__host__ __device__ inline size_t align16(size_t x) { return (x + 15) / 16 * 16; }
+
+// Runs body(chunk) for every chunk of the table on one CTA each (body may
+// sync the CTA): CTAs claim chunks from the launch's counter in table order,
+// one claim ahead.  Every CTA stops at its first claim past the table, so a
+// pass issues exactly nchunks + gridDim.x claims and base advances without a
+// read of the counter (the same accounting as for_each_group).
+template <typename F>
+__device__ __forceinline__ void for_each_chunk_cta(const SysDev &S, unsigned long long &base, F &&body) {
+    __shared__ int s_c;
+    const int nch = S.nchunks;
+    unsigned long long next = 0;
+    __syncthreads();   // s_c of an earlier pass is read
+    if (threadIdx.x == 0) next = atomicAdd(&S.ctl->claims, 1ull);
+    for (;;) {
+        if (threadIdx.x == 0) {
+            const unsigned long long v = next - base;
+            s_c = v < (unsigned long long)nch ? (int)v : nch;
+            if (s_c < nch) next = atomicAdd(&S.ctl->claims, 1ull);
+        }
+        __syncthreads();
+        const int c = s_c;
+        __syncthreads();   // s_c is rewritten by the next claim
+        if (c >= nch) break;
+        body(c);
+    }
+    base += (unsigned long long)nch + gridDim.x;
+}
+
+// Shared scratch of the sorted list layout: [chunk / 32 + 1][16] counts and
+// chunk 16-bit ranks.
+__host__ __device__ inline size_t sort_scratch_bytes(int chunk) {
+    return align16((size_t)(chunk / 32 + 1) * 16 * sizeof(int)) + align16((size_t)chunk * sizeof(uint16_t));
+}
+
+// Neighbour lists of one chunk in the sorted layout of the global-memory
+// shapes (the whole CTA).  A warp's pair loop runs as many list batches as
+// its longest list, so the chunk's slots are laid out in order of decreasing
+// batches -- estimated by each particle's list length at the previous
+// rebuild (cnt_id), the lists moving little between rebuilds -- with ties in
+// slot order: a counting sort over 16 batch classes, per 32-slot block a
+// warp match for the ranks, one exclusive scan in class-major order.  So
+// the layout is deterministic, and each particle's list (its pairs and
+// their order) is the same as in slot order: no force changes.
+template <typename T, int BLOCK>
+__device__ __forceinline__ void chunk_lists_sorted(const SysDev &S, int set, const int4 cd,
+                                                   unsigned char *scratch, int &over) {
+    using V = typename V2<T>::type;
+    const int tid = threadIdx.x, lane = tid & 31, n = cd.z - cd.y;
+    const int nwc = (n + 31) >> 5;
+    int *hist = reinterpret_cast<int *>(scratch);   // [nwc][16]: counts, then starts
+    uint16_t *rk = reinterpret_cast<uint16_t *>(scratch + align16((size_t)(n / 32 + 1) * 16 * sizeof(int)));
+    const V *npos = static_cast<const V *>(S.pos[set][0]);
+    const uint32_t *ncell = S.cell[set];
+    const int32_t *pid = S.pid[set];
+    const RepDev &R = S.reps[cd.x];
+    for (int i = tid; i < nwc * 16; i += BLOCK) hist[i] = 0;
+    __syncthreads();
+    for (int b0 = 0; b0 < n; b0 += BLOCK) {   // the same trip count on every thread
+        const int i = b0 + tid;
+        int cls = 16;                          // no slot
+        if (i < n) {
+            const int k = S.cnt_id[pid[cd.y + i]];
+            cls = 15 - min((k + NB_STAGE<T> - 1) / NB_STAGE<T>, 15);
+        }
+        const unsigned m = __match_any_sync(0xffffffffu, cls);
+        const int r = __popc(m & ((1u << lane) - 1u));
+        if (i < n) {
+            rk[i] = (uint16_t)(cls << 8 | r);
+            if (r == 0) hist[(i >> 5) * 16 + cls] = __popc(m);
+        }
+    }
+    __syncthreads();
+    if (tid < 32) {
+        // exclusive scan over (class, block) in class-major order, in place
+        int carry = 0;
+        for (int e0 = 0; e0 < 16 * nwc; e0 += 32) {
+            const int e = e0 + lane;
+            const int at = e < 16 * nwc ? (e % nwc) * 16 + e / nwc : 0;
+            const int v = e < 16 * nwc ? hist[at] : 0;
+            int incl = v;
+            for (int o = 1; o < 32; o <<= 1) {
+                const int t = __shfl_up_sync(0xffffffffu, incl, o);
+                if (lane >= o) incl += t;
+            }
+            if (e < 16 * nwc) hist[at] = carry + incl - v;
+            carry += __shfl_sync(0xffffffffu, incl, 31);
+        }
+    }
+    __syncthreads();
+    for (int i = tid; i < n; i += BLOCK) {
+        const int cls = rk[i] >> 8, r = rk[i] & 255;
+        const int q = cd.y + hist[(i >> 5) * 16 + cls] + r;
+        const int slot = cd.y + i;
+        const int cnt = build_list<T>(S, R, npos, ncell[slot], npos[slot], slot, q);
+        const int kept = cnt < S.K ? cnt : S.K;
+        S.nn[q] = kept | (i << 16);
+        S.cnt_id[pid[slot]] = kept;
+        over |= cnt > S.K;
+    }
+    __syncthreads();   // the scratch is reused by the next chunk
+}
+
 // ---------------------------------------------------------------- rebuild
 // With mode RB_ALL every particle gets its canonical cell (the MD cell its
 // offset now lies in, the offset re-expressed from that cell's corner); with
@@ -532,7 +640,8 @@ enum RebuildMode { RB_ALL = 1, RB_NONE = 2 };
 
 template <typename T, int BLOCK>
 __device__ bool rebuild(const SysDev &S, int &set, int &cur, unsigned &gen, int nloc,
-                        ChunkDesc *s_desc, int mode, unsigned long long &claim0) {
+                        ChunkDesc *s_desc, int mode, unsigned long long &claim0,
+                        unsigned char *sort_mem) {
     using V = typename V2<T>::type;
     Control *C = S.ctl;
     const GridBarrier bar{&C->bar_count, &C->bar_gen, &C->status};
@@ -678,29 +787,28 @@ __device__ bool rebuild(const SysDev &S, int &set, int &cur, unsigned &gen, int 
     set ^= 1;
     cur = 0;
     // R7: neighbour lists.  Staged shapes: the chunk windows and lists of
-    // the CTA's own chunks, read only by this CTA, so no barrier follows.
-    // Global-memory shapes: lists of groups taken from the dynamic
-    // distribution, which any warp may read next, so a barrier follows.
+    // the CTA's own chunks in slot order, read only by this CTA, so no
+    // barrier follows.  Global-memory shapes: chunks claimed by CTAs, lists
+    // in the sorted layout (chunk_lists_sorted); any warp may read them next,
+    // so a barrier follows.
     {
         const V *npos = static_cast<const V *>(S.pos[set][0]);
         const uint32_t *ncell = S.cell[set];
         int over = 0;
-        const auto list_of = [&](int slot, const RepDev &R) {
-            const int cnt = build_list<T>(S, R, npos, ncell[slot], npos[slot], slot);
-            S.nn[slot] = cnt < S.K ? cnt : S.K;
-            over |= cnt > S.K;
-        };
         if (S.stage) {
             for (int i = tid; i < nloc; i += BLOCK)
                 s_desc[i] = make_desc(S, ncell, own_chunk(i), WinParts<T>::value);
             __syncthreads();
             for (int i = 0; i < nloc; ++i)
-                for (int slot = s_desc[i].start + tid; slot < s_desc[i].end; slot += BLOCK)
-                    list_of(slot, S.reps[s_desc[i].rep]);
+                for (int slot = s_desc[i].start + tid; slot < s_desc[i].end; slot += BLOCK) {
+                    const int cnt = build_list<T>(S, S.reps[s_desc[i].rep], npos, ncell[slot], npos[slot],
+                                                  slot, slot);
+                    S.nn[slot] = cnt < S.K ? cnt : S.K;
+                    over |= cnt > S.K;
+                }
         } else {
-            for_each_group<BLOCK>(S, claim0, [&](const int4 &cd, int g0) {
-                const int slot = g0 + (tid & 31);
-                if (slot < cd.z) list_of(slot, S.reps[cd.x]);
+            for_each_chunk_cta(S, claim0, [&](int c) {
+                chunk_lists_sorted<T, BLOCK>(S, set, S.chunks[c], sort_mem, over);
             });
         }
         if (__syncthreads_or(over) && tid == 0) atomicOr(&C->status, (int)DS_NBR_OVERFLOW);
@@ -778,7 +886,6 @@ __device__ __forceinline__ void sample_particle(const SysDev &S, const RepDev &R
 
 // Dynamic shared memory of the persistent kernel: sampling histograms,
 // chunk descriptors, two staging buffers (window positions, own velocities).
-__host__ __device__ inline size_t align16(size_t x) { return (x + 15) / 16 * 16; }
 __host__ __device__ inline size_t smem_hist_bytes(int n_lg, int n_dx, int nb) {
     return align16((size_t)n_lg * n_dx * nb * sizeof(int));
 }
@@ -807,7 +914,7 @@ __host__ __device__ inline size_t smem_bytes(int n_lg, int n_dx, int nb, int chu
     // the two staging buffers exist only when chunks are staged in shared
     // memory; without them more CTAs fit on an SM
     return smem_hist_bytes(n_lg, n_dx, nb) + align16(MAX_CPC * sizeof(ChunkDesc)) +
-           (staged ? 2 * stage_bytes<T>(chunk) : 0);
+           (staged ? 2 * stage_bytes<T>(chunk) : sort_scratch_bytes(chunk));
 }
 
 // Records the force of one slot by particle id (md_step_forces only).
@@ -911,7 +1018,7 @@ __global__ void __launch_bounds__(BLOCK, md_min_ctas(BLOCK, DENSE)) k_md_persist
     if (force_rebuild) {
         // RB_ALL: canonical cells (a new state); RB_NONE: sort and lists of a
         // state written in another order, no particle's cell moved
-        if (!rebuild<T, BLOCK>(S, set, cur, gen, nloc, s_desc, force_rebuild, claim0)) return;
+        if (!rebuild<T, BLOCK>(S, set, cur, gen, nloc, s_desc, force_rebuild, claim0, stg)) return;
         if (force_rebuild == RB_ALL) disp = 0.0;
     } else {
         for (int i = tid; i < nloc; i += BLOCK)
@@ -977,15 +1084,24 @@ __global__ void __launch_bounds__(BLOCK, md_min_ctas(BLOCK, DENSE)) k_md_persist
             // dynamic distribution (for_each_group)
             const ChunkDesc none{};
             for_each_group<BLOCK>(S, claim0, [&](const int4 &cd, int g0) {
-                const int slot = g0 + lane;
-                if (slot >= cd.z) return;
+                // sorted layout: position q holds the list and count of the
+                // slot its count word names; the first list batch is read
+                // with the count, the slot's state once it arrives
+                const int q = g0 + lane;
+                if (q >= cd.z) return;
+                uint32_t e[NB_STAGE<T>];
+                const uint32_t *lst = S.nbr + (long long)(q >> 5) * S.K * 32 + (q & 31);
+#pragma unroll
+                for (int u = 0; u < NB_STAGE<T>; ++u) e[u] = lst[u * 32];
+                const int w = S.nn[q];
+                const int slot = cd.y + (w >> 16);
                 const RepDev &R = S.reps[cd.x];
                 const T hk = rd<T>(R.hk, R.hkf), dt = rd<T>(R.dt, R.dtf);
                 const float vscale = (float)(R.dt / R.half_skin);
                 const V oi = pin[slot];
                 const V vi = vel[slot];   // requested now, used after the force sum
                 T fx = T(0), fy = T(0);
-                lj_list<T>(S, R, none, nullptr, nullptr, pin, oi, slot, S.nn[slot], fx, fy);
+                lj_list_from<T>(S, R, none, nullptr, pin, oi, q, w & 0xffff, e, fx, fy);
                 if (S.dbg_fx && it == nsteps - 1) debug_force(S, set, slot, fx, fy);
                 kick_drift<T>(R, oi, vi, fx, fy, hk, dt, first, vscale, pout, vel, slot, vm, bad);
             });
@@ -1062,7 +1178,7 @@ __global__ void __launch_bounds__(BLOCK, md_min_ctas(BLOCK, DENSE)) k_md_persist
             }
         }
         if (disp >= 1.0) {
-            if (!rebuild<T, BLOCK>(S, set, cur, gen, nloc, s_desc, RB_ALL, claim0)) return;
+            if (!rebuild<T, BLOCK>(S, set, cur, gen, nloc, s_desc, RB_ALL, claim0, stg)) return;
             disp = 0.0;
         }
         __syncthreads();   // s_due / s_win / s_vmax are rewritten in the next step
