@@ -731,21 +731,28 @@ __device__ bool rebuild(const SysDev &S, int &set, int &cur, unsigned &gen, int 
     }
     for (int c = s0 + tid; c < s1; c += BLOCK) S.cellcnt[c] = 0;
     if (!grid_sync(bar, gen, S.timeout_ns)) return false;
-    // R5: order each cell's particles by id; restore the padding-cell counts
+    // R5: order each cell's particles by id, each cell by the CTA whose own
+    // chunk holds the cell's first slot (so the work follows the particles,
+    // not the cells, of which dilute replicas have many empty ones); restore
+    // the padding-cell counts
     {
         const int32_t *pid = S.pid[set];
-        for (int c = s0 + tid; c < s1; c += BLOCK) {
-            const int a = S.cell_start[c], b = S.cell_start[c + 1];
-            if (b - a < 2 || S.perm[a] < 0) continue;
-            for (int i = a + 1; i < b; ++i) {
-                const int pi = S.perm[i];
-                const int key = pid[pi];
-                int k = i - 1;
-                while (k >= a && pid[S.perm[k]] > key) {
-                    S.perm[k + 1] = S.perm[k];
-                    --k;
+        for (int i = 0; i < nloc; ++i) {
+            const int4 cd = S.chunks[own_chunk(i)];
+            for (int p = cd.y + tid; p < cd.z; p += BLOCK) {
+                const int c = S.newcell[S.perm[p]];
+                const int a = S.cell_start[c], b = S.cell_start[c + 1];
+                if (a != p || b - a < 2) continue;
+                for (int j = a + 1; j < b; ++j) {
+                    const int pj = S.perm[j];
+                    const int key = pid[pj];
+                    int k = j - 1;
+                    while (k >= a && pid[S.perm[k]] > key) {
+                        S.perm[k + 1] = S.perm[k];
+                        --k;
+                    }
+                    S.perm[k + 1] = pj;
                 }
-                S.perm[k + 1] = pi;
             }
         }
         for (int r = blockIdx.x * BLOCK + tid; r < S.nrep; r += gridDim.x * BLOCK) {
