@@ -9,7 +9,9 @@ generator), against what the definition fixes:
   * with two blocks of unequal windows the four equally likely resamples
     are known: the bootstrap standard deviation tends to theirs;
   * symmetric-set averaging of identical set members changes nothing;
-  * the block indices drawn are uniform and consecutive draws uncorrelated.
+  * the block indices drawn are uniform and consecutive draws uncorrelated;
+  * the draws of seed 0 are the published first outputs of SplitMix64 from
+    state 0 (tests/golden/splitmix64_state0.txt).
 """
 
 import numpy as np
@@ -79,3 +81,13 @@ def test_draws_uniform_and_uncorrelated(orc):
     u = (x >> np.uint64(11)).astype(np.float64) / 2.0 ** 53
     r = np.corrcoef(u[:-1], u[1:])[0, 1]
     assert abs(r) < 5.0 / np.sqrt(len(u))
+
+
+def test_draws_match_published_splitmix64(orc):
+    import os
+
+    path = os.path.join(os.path.dirname(__file__), "golden", "splitmix64_state0.txt")
+    rows = [ln.split() for ln in open(path) if ln.strip() and not ln.startswith("#")]
+    assert len(rows) == 3
+    for c, v in rows:
+        assert orc.splitmix64(0, int(c)) == int(v, 16), (c, v)
