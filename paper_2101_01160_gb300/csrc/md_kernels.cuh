@@ -474,8 +474,13 @@ __device__ __forceinline__ void lj_list_from(const SysDev &S, const RepDev &R, c
     const T rc2 = rd<T>(R.rc2, R.rc2f);
     const T eps24 = T(24) * rd<T>(R.eps, R.epsf);
     const T sig2 = rd<T>(R.sig2, R.sig2f);
-    const T sxs[3] = {-h - oi.x, -oi.x, h - oi.x};
-    const T sys[3] = {-h - oi.y, -oi.y, h - oi.y};
+    // the shift of a neighbour in column (row) tag t is (t - 1) h - offset:
+    // one FMA of the exact factor t - 1 (from the float bits of 2^23 + t,
+    // no conversion instruction), the product exact, so the value is the
+    // correctly rounded sum the other force paths select from -h - off,
+    // -off and h - off (a zero may differ in sign, which moves nothing);
+    // two registers instead of six
+    const T nox = -oi.x, noy = -oi.y;
     const uint32_t *lst = S.nbr + (long long)(self >> 5) * S.K * 32 + (self & 31);
     double pe_unused = 0.0, fa_unused = 0.0;
     constexpr int U = NB_STAGE<T>;
@@ -496,8 +501,10 @@ __device__ __forceinline__ void lj_list_from(const SysDev &S, const RepDev &R, c
                 w = w < 0 ? w + R.n : (w >= R.n ? w - R.n : w);
                 const typename V2<T>::type o = (d.ok && w < d.npw) ? spos[w] : pin[j];
                 const uint32_t ox = (e[u] >> 28) & 3u, oy = e[u] >> 30;
-                const T sx = ox == 0 ? sxs[0] : (ox == 1 ? sxs[1] : sxs[2]);
-                const T sy = oy == 0 ? sys[0] : (oy == 1 ? sys[1] : sys[2]);
+                const float kx = __int_as_float(0x4b000000u | ox) - 8388609.0f;   // ox - 1
+                const float ky = __int_as_float(0x4b000000u | oy) - 8388609.0f;
+                const T sx = fmaT((T)kx, h, nox);
+                const T sy = fmaT((T)ky, h, noy);
                 lj_pair_acc<T, false>(o.x + sx, o.y + sy, rc2, eps24, sig2, fx, fy, 0.0, pe_unused,
                                       fa_unused);
             }
@@ -1103,12 +1110,13 @@ __global__ void __launch_bounds__(BLOCK, md_min_ctas(BLOCK, DENSE)) k_md_persist
                 const int w = S.nn[q];
                 const int slot = cd.y + (w >> 16);
                 const RepDev &R = S.reps[cd.x];
-                const T hk = rd<T>(R.hk, R.hkf), dt = rd<T>(R.dt, R.dtf);
-                const float vscale = (float)(R.dt / R.half_skin);
                 const V oi = pin[slot];
                 const V vi = vel[slot];   // requested now, used after the force sum
                 T fx = T(0), fy = T(0);
                 lj_list_from<T>(S, R, none, nullptr, pin, oi, q, w & 0xffff, e, fx, fy);
+                // the kick's constants only now: fewer values live in the pair loop
+                const T hk = rd<T>(R.hk, R.hkf), dt = rd<T>(R.dt, R.dtf);
+                const float vscale = (float)(R.dt / R.half_skin);
                 if (S.dbg_fx && it == nsteps - 1) debug_force(S, set, slot, fx, fy);
                 kick_drift<T>(R, oi, vi, fx, fy, hk, dt, first, vscale, pout, vel, slot, vm, bad);
             });
