@@ -1111,10 +1111,12 @@ __global__ void __launch_bounds__(BLOCK, md_min_ctas(BLOCK, DENSE)) k_md_persist
                 const int slot = cd.y + (w >> 16);
                 const RepDev &R = S.reps[cd.x];
                 const V oi = pin[slot];
-                const V vi = vel[slot];   // requested now, used after the force sum
                 T fx = T(0), fy = T(0);
                 lj_list_from<T>(S, R, none, nullptr, pin, oi, q, w & 0xffff, e, fx, fy);
-                // the kick's constants only now: fewer values live in the pair loop
+                // the velocity and the kick's constants only now: fewer values
+                // live in the pair loop of the 32-register budget (measured:
+                // faster than requesting the velocity before the sum)
+                const V vi = vel[slot];
                 const T hk = rd<T>(R.hk, R.hkf), dt = rd<T>(R.dt, R.dtf);
                 const float vscale = (float)(R.dt / R.half_skin);
                 if (S.dbg_fx && it == nsteps - 1) debug_force(S, set, slot, fx, fy);
