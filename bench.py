@@ -48,7 +48,7 @@ W = 4
 # lists hold pairs within rc + skin and are rebuilt when a displacement
 # reaches skin/2; results do not depend on it).  Measured on this ensemble:
 # 0.35-0.45 take about 77 ms per 400 steps, 0.5 about 80, 0.6 82, 0.8 86.
-SKIN = 0.4
+SKIN = 0.6   # Verlet skin of the ensemble (measured sweep, see the MD kernel's profile)
 BYTES_PER_PARTICLE_STEP = 40.0      # FP32 cell + offset: 20 B state read + 20 B written
 RESIDENT_SLAB_PARTICLES = 8192      # own particles one resident slab (one SM's shared memory) holds
 L2_BYTES = 129 * 2 ** 20
@@ -71,11 +71,12 @@ def _peaks(key="hbm_gbs", fallback=6800.0):
 # of k_md_persistent<float,256,1> (the launch shape the autotuner picks),
 # copied here with its provenance; it is reported only for that kernel and
 # launch shape, and must be re-measured when the kernel changes.
-MD_TRAFFIC = {"kernel": "k_md_persistent<float,256,1>", "bytes_per_launch": 180913173709,
+MD_TRAFFIC = {"kernel": "k_md_persistent<float,256,1>", "bytes_per_launch": 182888381133,
               "source": "ncu --metrics dram__bytes_read.sum,dram__bytes_write.sum,gpu__time_duration.sum "
                         "over every launch of 'bench.py --steps 2 --warmup 3 --no-cpu-baseline "
                         "--no-variants' (one pass), mean of the five 400-step launches of warm-up "
-                        "and timed region: 127.9 GB read + 53.0 GB written, 79.2 B per particle-step"}
+                        "and timed region (Verlet skin 0.6): 132.8 GB read + 50.1 GB written, 80.1 B "
+                        "per particle-step"}
 
 
 def _cpu_model():
