@@ -246,6 +246,41 @@ def _time_surrogate(mdlg, torch, n=1 << 20, reps=20):
             "kernel": "k_mlp_fused", "workload": "1,048,576 queries uniform in the training box"}
 
 
+def _time_surrogate_training(mdlg, torch, batch=8192, reps=20):
+    """One Adam training step of the f_eq surrogate (forward, KL loss and
+    backward GEMMs on the tensor cores, Adam update) on a batch of synthetic
+    queries and target distributions; algorithmic flops 3x the forward's per
+    sample (forward, input gradient, weight gradient)."""
+    from paper_2101_01160_gb300 import inputs, surrogate
+
+    model = surrogate.new_model(1)
+    X = torch.from_numpy(inputs.surrogate_queries(batch, 5, lo=(0.02, 1.0, 0.05, 1.0),
+                                                  hi=(0.30, 20.0, 0.2, 4.0))).cuda()
+    g = torch.Generator(device="cuda")
+    g.manual_seed(6)
+    T = torch.rand((batch, model.n_classes), device="cuda", generator=g)
+    T = (T / T.sum(dim=1, keepdim=True)).contiguous()
+    loss = torch.zeros(1, dtype=torch.float32, device="cuda")
+    for _ in range(3):
+        model.train_step(X, T, 1e-4, loss=loss)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(reps):
+        model.train_step(X, T, 1e-4, loss=loss)
+    e1.record()
+    torch.cuda.synchronize()
+    model.status()
+    ms = e0.elapsed_time(e1) / reps
+    sizes = mdlg.SURR_SIZES
+    flop = 3 * 2.0 * sum(a * b for a, b in zip(sizes[:-1], sizes[1:])) * batch
+    peak, kind = _peaks("bf16_tflops", 1900.0)
+    tf = flop / (ms * 1e-3) / 1e12
+    return {"batch": batch, "ms_per_step": ms, "samples_per_s": batch / (ms * 1e-3), "tflops": tf,
+            "bf16_peak_tflops": peak, "peak_kind": kind, "frac": tf / peak,
+            "workload": "Adam steps on 8192 synthetic (query, distribution) pairs, steps queued back to back"}
+
+
 def _time_queued(torch, fn, reps=20):
     """Device time of one launch of fn with a cold L2: reps x (256 MB L2
     flush + fn) queued back to back between two CUDA events, less reps
@@ -514,6 +549,7 @@ def run_ours(args):
                            "frac_of_bound": v64["value"] / min(hbm_ps, alu_ps)}
         variants["equal_accuracy"] = _equal_accuracy(mdlg, torch)
         variants["surrogate_inference"] = _time_surrogate(mdlg, torch)
+        variants["surrogate_training"] = _time_surrogate_training(mdlg, torch)
         variants["disp_hist"] = _time_disp_hist(mdlg, torch)
         variants["local_fields"] = _time_local_fields(mdlg, torch)
 

@@ -26,6 +26,7 @@ using bf16 = __nv_bfloat16;
 
 constexpr int GBM = 128;   // GEMM tile rows (TMEM lanes)
 constexpr int GBK = 64;    // K per pipeline stage
+constexpr int GRAD_MAX_SPLIT = 64;   // K splits of a weight-gradient GEMM (K = the batch)
 constexpr uint64_t GEMM_WAIT_NS = 2000000000ull;
 
 enum Epi { EPI_F32 = 0, EPI_BIAS_F32 = 1, EPI_BIAS_SILU = 2, EPI_DSILU = 3 };
@@ -36,6 +37,7 @@ struct GemmArgs {
     int lda, ldb, M, N, K;
     float *C;           // FP32 output (EPI_F32 / EPI_BIAS_F32; pre-activation for EPI_BIAS_SILU)
     int ldc;
+    long long c_split;  // EPI_F32 split over K (grid.y = z): K range z of length K, tile at C + z c_split
     bf16 *H;            // BF16 output (activation or gradient)
     int ldh;
     const float *bias;  // [N]
@@ -90,6 +92,8 @@ __global__ void __launch_bounds__(128) k_gemm(GemmArgs g) {
     const uint32_t tmem = *s_tmem;
     const int m0 = blockIdx.x * GBM;
     const int nk = g.K / GBK;
+    const int kb = (int)blockIdx.y * nk;   // first stage of this CTA's K range
+    const int n0 = (int)blockIdx.z * N;    // first output column of this CTA (N split)
     const uint32_t idesc = umma::idesc_bf16(GBM, N);
     for (int kt = 0; kt < nk; ++kt) {
         const int s = kt & 1;
@@ -100,11 +104,11 @@ __global__ void __launch_bounds__(128) k_gemm(GemmArgs g) {
         if (!s_ok) break;
         for (int c = tid; c < GBM * 8; c += 128) {
             const int r = c >> 3, k8 = c & 7;
-            cpa16(sa + tile_off(r, k8), g.A + (size_t)(m0 + r) * g.lda + kt * GBK + k8 * 8);
+            cpa16(sa + tile_off(r, k8), g.A + (size_t)(m0 + r) * g.lda + (kb + kt) * GBK + k8 * 8);
         }
         for (int c = tid; c < N * 8; c += 128) {
             const int r = c >> 3, k8 = c & 7;
-            cpa16(sb + tile_off(r, k8), g.B + (size_t)r * g.ldb + kt * GBK + k8 * 8);
+            cpa16(sb + tile_off(r, k8), g.B + (size_t)(n0 + r) * g.ldb + (kb + kt) * GBK + k8 * 8);
         }
         asm volatile("cp.async.commit_group;" ::: "memory");
         asm volatile("cp.async.wait_group 0;" ::: "memory");
@@ -135,11 +139,12 @@ __global__ void __launch_bounds__(128) k_gemm(GemmArgs g) {
     umma::fence_after();
     if (s_ok) {
         const int row = m0 + warp * 32 + lane;
-        for (int c0 = 0; c0 < N; c0 += 16) {
+        for (int cl = 0; cl < N; cl += 16) {
             float v[16];
-            umma::ld16(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0, v);
+            umma::ld16(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)cl, v);
+            const int c0 = n0 + cl;   // output column
             if (EPI == EPI_F32 || EPI == EPI_BIAS_F32) {
-                float4 *dst = reinterpret_cast<float4 *>(g.C + (size_t)row * g.ldc + c0);
+                float4 *dst = reinterpret_cast<float4 *>(g.C + (size_t)blockIdx.y * g.c_split + (size_t)row * g.ldc + c0);
 #pragma unroll
                 for (int q = 0; q < 4; ++q) {
                     float4 o;
@@ -178,13 +183,25 @@ __global__ void __launch_bounds__(128) k_gemm(GemmArgs g) {
 
 size_t gemm_smem(int N) { return 2 * (size_t)(GBM * GBK * 2 + N * GBK * 2) + 32; }
 
+// ksplit > 1 (EPI_F32 only): g.K is one split's K; split z writes its
+// partial tile to C + z c_split, to be summed in split order.  A GEMM with
+// fewer 128-row tiles than the device has SMs is also split over N into two
+// column blocks of N/2 (grid.z), each CTA with its own accumulator; the
+// arithmetic of every output is the same.
 template <int EPI>
-int gemm_launch(const GemmArgs &g, cudaStream_t st) {
+int gemm_launch(const GemmArgs &g, cudaStream_t st, int ksplit = 1) {
     if (g.M % GBM || g.K % GBK || g.N % 16 || g.N < 16 || g.N > 256 || g.lda % 8 || g.ldb % 8)
         return fail(MD_E_ARG, "gemm: M %% 128, K %% 64, N %% 16 in [16,256], lda/ldb %% 8 required");
-    const size_t smem = gemm_smem(g.N);
+    if (ksplit < 1 || (ksplit > 1 && EPI != EPI_F32)) return fail(MD_E_ARG, "gemm: K split only for EPI_F32");
+    int dev = 0, nsm = 0;
+    MD_CUDA_TRY(cudaGetDevice(&dev));
+    MD_CUDA_TRY(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+    const int nsplit = (g.N % 32 == 0 && (long long)(g.M / GBM) * ksplit < nsm) ? 2 : 1;
+    GemmArgs gg = g;
+    gg.N = g.N / nsplit;
+    const size_t smem = gemm_smem(gg.N);
     MD_CUDA_TRY(cudaFuncSetAttribute(k_gemm<EPI>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    k_gemm<EPI><<<g.M / GBM, 128, smem, st>>>(g);
+    k_gemm<EPI><<<dim3(g.M / GBM, ksplit, nsplit), 128, smem, st>>>(gg);
     MD_CUDA_TRY(cudaGetLastError());
     return MD_OK;
 }
@@ -271,22 +288,42 @@ __global__ void k_transpose(const bf16 *in, int R, int C, bf16 *out) {
 }
 
 // Column sums of a BF16 [M][N] matrix in FP32 (fixed order), into out[n].
-__global__ void k_colsum(const bf16 *a, int M, int N, int ld, float *out) {
+// Reductions over the batch in two passes with a fixed order: partial sums
+// over chunks of GRAD_ROWS rows (grid.y = chunk), then the chunks summed in
+// chunk order (k_sum_parts), so that the batch is spread over many CTAs and
+// the result does not depend on the launch.
+constexpr int GRAD_ROWS = 128;
+
+// part[chunk][n] = sum of column n of a [M][ld] BF16 matrix over the chunk.
+__global__ void k_colsum_part(const bf16 *a, int M, int N, int ld, float *part) {
     const int n = blockIdx.x * blockDim.x + threadIdx.x;
     if (n >= N) return;
+    const int m0 = blockIdx.y * GRAD_ROWS, m1 = min(M, m0 + GRAD_ROWS);
     float s = 0.f;
-    for (int m = 0; m < M; ++m) s += __bfloat162float(a[(size_t)m * ld + n]);
-    out[n] = s;
+    for (int m = m0; m < m1; ++m) s += __bfloat162float(a[(size_t)m * ld + n]);
+    part[(size_t)blockIdx.y * N + n] = s;
 }
 
-// dW_1 = dZ_1^T x_f (4 inputs), fixed summation order over the batch.
-__global__ void k_grad_layer1(const bf16 *dZ, int M, int width, const float *xf, float *gW) {
+// dW_1 = dZ_1^T x_f (4 inputs): part[chunk][o * 4 + k] over the chunk's rows.
+__global__ void k_grad_layer1_part(const bf16 *dZ, int M, int width, const float *xf, float *part) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= width * 4) return;
     const int o = i / 4, k = i % 4;
+    const int m0 = blockIdx.y * GRAD_ROWS, m1 = min(M, m0 + GRAD_ROWS);
     float s = 0.f;
-    for (int m = 0; m < M; ++m) s += __bfloat162float(dZ[(size_t)m * width + o]) * xf[4 * m + k];
-    gW[i] = s;
+    for (int m = m0; m < m1; ++m) s += __bfloat162float(dZ[(size_t)m * width + o]) * xf[4 * m + k];
+    part[(size_t)blockIdx.y * width * 4 + i] = s;
+}
+
+// out[r][c] = sum over z = 0 .. nz-1, in z order, of part[z stride + r ldp + c].
+__global__ void k_sum_parts(const float *part, int nz, long long stride, int rows, int cols, int ldp,
+                            float *out, int ldo) {
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= (long long)rows * cols) return;
+    const int r = (int)(i / cols), c = (int)(i % cols);
+    float s = 0.f;
+    for (int z = 0; z < nz; ++z) s += part[z * stride + (long long)r * ldp + c];
+    out[(long long)r * ldo + c] = s;
 }
 
 // Adam on FP32 master parameters; refreshes the BF16 copy (and its
@@ -749,6 +786,7 @@ struct mlp_model {
     std::vector<float *> Z;       // [cap][width] per hidden layer
     std::vector<bf16 *> H;        // [cap][width] per hidden layer
     bf16 *dA = nullptr, *dB = nullptr, *dlog = nullptr, *tA = nullptr, *tB = nullptr;
+    float *part = nullptr;        // partial sums of the batch reductions of the gradients
     int *status = nullptr;
     std::vector<void *> allocs, ws;
 };
@@ -787,6 +825,8 @@ int ensure_ws(mlp_model *m, long long rows) {
     A((void **)&m->dlog, R * m->npad * sizeof(bf16));
     A((void **)&m->tA, R * Wd * sizeof(bf16));
     A((void **)&m->tB, R * Wd * sizeof(bf16));
+    A((void **)&m->part, std::max((size_t)GRAD_MAX_SPLIT * Wd * Wd,
+                                  ((size_t)rows / GRAD_ROWS + 1) * Wd * 4) * sizeof(float));
     if (rc) return rc;
     m->cap = rows;
     return MD_OK;
@@ -841,6 +881,15 @@ int forward(mlp_model *m, const float *X, long long M, long long Mpad, bool keep
     return MD_OK;
 }
 
+// Column sums of dZ [M][N] (bias gradient) over the batch, two passes.
+int colsum(const bf16 *dZ, int M, int N, float *part, float *out, cudaStream_t st) {
+    const int nch = (M + GRAD_ROWS - 1) / GRAD_ROWS;
+    k_colsum_part<<<dim3((N + 127) / 128, nch), 128, 0, st>>>(dZ, M, N, N, part);
+    k_sum_parts<<<(N + 255) / 256, 256, 0, st>>>(part, nch, N, 1, N, N, out, N);
+    MD_CUDA_TRY(cudaGetLastError());
+    return MD_OK;
+}
+
 int transpose(const bf16 *in, int R, int C, bf16 *out, cudaStream_t st) {
     dim3 tb(32, 8), gr((C + 31) / 32, (R + 31) / 32);
     k_transpose<<<gr, tb, 0, st>>>(in, R, C, out);
@@ -876,12 +925,26 @@ int backward(mlp_model *m, const float *X, const float *T, int Mb, float *loss_d
         g.M = dzw;
         g.N = m->width;
         g.K = Mb;
-        g.C = m->gW[l];
         g.ldc = m->in[l];
         g.status = m->status;
-        if ((rc = gemm_launch<EPI_F32>(g, st))) return rc;
-        k_colsum<<<(dzw + 127) / 128, 128, 0, st>>>(dZ, Mb, dzw, dzw, m->gb[l]);
-        MD_CUDA_TRY(cudaGetLastError());
+        // K = the batch: split over up to GRAD_MAX_SPLIT CTAs per tile row
+        // (two stages each at least), partial tiles summed in split order
+        const int nkt = Mb / GBK;
+        int ks = 1;
+        while (ks * 2 <= GRAD_MAX_SPLIT && nkt % (ks * 2) == 0 && nkt / (ks * 2) >= 2) ks *= 2;
+        if (ks == 1) {
+            g.C = m->gW[l];
+            if ((rc = gemm_launch<EPI_F32>(g, st))) return rc;
+        } else {
+            g.K = Mb / ks;
+            g.C = m->part;
+            g.c_split = (long long)dzw * g.ldc;
+            if ((rc = gemm_launch<EPI_F32>(g, st, ks))) return rc;
+            const long long n = (long long)dzw * m->width;
+            k_sum_parts<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(m->part, ks, g.c_split, dzw, m->width, g.ldc,
+                                                                    m->gW[l], g.ldc);
+        }
+        if ((rc = colsum(dZ, Mb, dzw, m->part, m->gb[l], st))) return rc;
         // dZ_{l-1} = (dZ W_l) * silu'(Z_{l-1})
         GemmArgs d{};
         d.A = dZ;
@@ -900,10 +963,12 @@ int backward(mlp_model *m, const float *X, const float *T, int Mb, float *loss_d
         dZ = bufs[l & 1];
         dzw = m->width;
     }
-    k_grad_layer1<<<(m->width * 4 + 127) / 128, 128, 0, st>>>(dZ, Mb, m->width, m->xf, m->gW[0]);
-    k_colsum<<<(m->width + 127) / 128, 128, 0, st>>>(dZ, Mb, m->width, m->width, m->gb[0]);
+    const int nch = (Mb + GRAD_ROWS - 1) / GRAD_ROWS;
+    k_grad_layer1_part<<<dim3((m->width * 4 + 127) / 128, nch), 128, 0, st>>>(dZ, Mb, m->width, m->xf, m->part);
+    k_sum_parts<<<(m->width * 4 + 255) / 256, 256, 0, st>>>(m->part, nch, (long long)m->width * 4, 1,
+                                                            m->width * 4, m->width * 4, m->gW[0], m->width * 4);
     MD_CUDA_TRY(cudaGetLastError());
-    return MD_OK;
+    return colsum(dZ, Mb, m->width, m->part, m->gb[0], st);
 }
 
 
