@@ -372,7 +372,8 @@ def run_profile_case(args):
     launch shape (256 threads, 1 chunk per thread, global staging with the
     full-occupancy register budget, as the autotuner picks for the bench), two
     400-step warm-up launches then three 100-step launches; mlp = three fused
-    surrogate forward passes on 1M queries; disp = eight displacement-PDF
+    surrogate forward passes on 1M queries; train = four surrogate training
+    steps on 8192 synthetic samples; disp = eight displacement-PDF
     histograms of a 16.8M-particle snapshot pair; local = the occupation and
     collision kernels of the local fields on a 6.4M-particle ensemble snapshot
     pair (two occupation calls, then three occupation + collision pairs)."""
@@ -393,6 +394,23 @@ def run_profile_case(args):
         print(json.dumps({"profile_case": "res16", "n_particles": int(sum(e[0] for e in ens)),
                           "rebuilds": int(s.info().n_rebuilds)}))
         s.close()
+    elif args.profile_case == "train":
+        from paper_2101_01160_gb300 import inputs, surrogate
+
+        model = surrogate.new_model(1)
+        B = 8192
+        X = torch.from_numpy(inputs.surrogate_queries(B, 5, lo=(0.02, 1.0, 0.05, 1.0),
+                                                      hi=(0.30, 20.0, 0.2, 4.0))).cuda()
+        g = torch.Generator(device="cuda")
+        g.manual_seed(6)
+        T = torch.rand((B, model.n_classes), device="cuda", generator=g)
+        T = (T / T.sum(dim=1, keepdim=True)).contiguous()
+        loss = torch.zeros(1, dtype=torch.float32, device="cuda")
+        for _ in range(4):
+            model.train_step(X, T, 1e-4, loss=loss)
+        torch.cuda.synchronize()
+        model.status()
+        print(json.dumps({"profile_case": "train", "batch": B, "loss": float(loss.item())}))
     elif args.profile_case == "md64":
         ens = ensemble(reps=range(64))
         cat = [np.concatenate([getattr(e[4], f) for e in ens]) for f in ("x", "y", "vx", "vy")]
@@ -760,7 +778,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-variants", action="store_true")
-    ap.add_argument("--profile-case", choices=["md64", "res16", "mlp", "disp", "local"], default=None,
+    ap.add_argument("--profile-case", choices=["md64", "res16", "mlp", "train", "disp", "local"], default=None,
                     help="run a small case for ncu captures instead of the bench")
     args = ap.parse_args()
     if args.profile_case:
