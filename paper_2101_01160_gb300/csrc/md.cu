@@ -612,6 +612,7 @@ RepDev make_rep(const md_params &q, int prec, int n_dx) {
     for (int d = 0; d < n_dx; ++d) {
         R.lx[d] = q.lx[d];
         R.dxl[d] = R.L / (double)q.lx[d];
+        R.dxl_invf[d] = (float)(1.0 / R.dxl[d]);
     }
     R.hf = (float)h;
     R.dtf = (float)R.dt;

@@ -51,6 +51,7 @@ struct RepDev {
     double h, L, dt, hk, rc2, eps, sig2, vshift, mass;
     double rv2, half_skin;         // Verlet radius^2, rebuild displacement bound
     double dxl[MD_MAX_DX];
+    float dxl_invf[MD_MAX_DX];     // RN32(1 / dxl): the FP32 lattice-cell decision
     float hf, dtf, hkf, rc2f, epsf, sig2f, rv2f;
 };
 
@@ -879,15 +880,18 @@ __device__ __forceinline__ void sample_particle(const SysDev &S, const RepDev &R
         const double ex2 = ex * ex, ey2 = ey * ey;
         m2 = ex2 + ey2;
         m4 = ex2 * ex2 + ey2 * ey2;
-        const double x1 = cell_position(cx, R.h, (double)on.x);
-        const double y1 = cell_position(cy, R.h, (double)on.y);
-        const double x0 = cell_position(scx, R.h, (double)so.x);
-        const double y0 = cell_position(scy, R.h, (double)so.y);
+        // lattice cells floor(RN(RN(c h + off) / dxl)) mod lx, decided in FP32
+        // where that provably gives the same cell (lattice_cell_f32)
         for (int d = 0; d < S.n_dx; ++d) {
             const int lx = R.lx[d];
             const double dxl = R.dxl[d];
-            const long long ddx = lattice_shift(lattice_cell(x1, dxl, lx) - lattice_cell(x0, dxl, lx), lx);
-            const long long ddy = lattice_shift(lattice_cell(y1, dxl, lx) - lattice_cell(y0, dxl, lx), lx);
+            const float invf = R.dxl_invf[d];
+            const int ddx = lattice_shift_near(lattice_cell_f32<T>(cx, on.x, R.h, R.hf, dxl, invf, lx) -
+                                                   lattice_cell_f32<T>(scx, so.x, R.h, R.hf, dxl, invf, lx),
+                                               lx);
+            const int ddy = lattice_shift_near(lattice_cell_f32<T>(cy, on.y, R.h, R.hf, dxl, invf, lx) -
+                                                   lattice_cell_f32<T>(scy, so.y, R.h, R.hf, dxl, invf, lx),
+                                               lx);
             if (ddx >= -S.W && ddx <= S.W && ddy >= -S.W && ddy <= S.W)
                 bins[d] = (int)((ddy + S.W) * (2 * S.W + 1) + (ddx + S.W));
             else
