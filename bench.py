@@ -71,11 +71,11 @@ def _peaks(key="hbm_gbs", fallback=6800.0):
 # of k_md_persistent<float,256,1> (the launch shape the autotuner picks),
 # copied here with its provenance; it is reported only for that kernel and
 # launch shape, and must be re-measured when the kernel changes.
-MD_TRAFFIC = {"kernel": "k_md_persistent<float,256,1>", "bytes_per_launch": 182888381133,
+MD_TRAFFIC = {"kernel": "k_md_persistent<float,256,1>", "bytes_per_launch": 182509082266,
               "source": "ncu --metrics dram__bytes_read.sum,dram__bytes_write.sum,gpu__time_duration.sum "
                         "over every launch of 'bench.py --steps 2 --warmup 3 --no-cpu-baseline "
                         "--no-variants' (one pass), mean of the five 400-step launches of warm-up "
-                        "and timed region (Verlet skin 0.6): 132.8 GB read + 50.1 GB written, 80.1 B "
+                        "and timed region (Verlet skin 0.6): 132.7 GB read + 49.8 GB written, 79.9 B "
                         "per particle-step"}
 
 
