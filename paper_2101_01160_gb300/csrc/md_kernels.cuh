@@ -15,13 +15,19 @@
 //     sets; a rebuild gathers the sorted particles from one set into the
 //     other.
 //   * work is cut into chunks of ppt*BLOCK consecutive slots of one replica,
-//     dealt to CTAs round-robin for the whole launch.
+//     in a table ordered by decreasing estimated cost; the first rounds of
+//     the table are dealt to CTAs round-robin, the rest claimed at run time
+//     (for_each_group); the sort phases and the sampling pass deal all of
+//     them round-robin.
 //   * Verlet neighbour lists (all particles within rv = rc + skin at the last
 //     rebuild, in cell-stencil order), ELL layout interleaved by 32-slot
-//     groups: entry k of slot i is nbr[(i/32)*K*32 + k*32 + i%32], so a warp
-//     reads one entry for all its lanes in one coalesced access.  An entry
-//     packs the neighbour's slot and its cell offset (dcx+1, dcy+1).  The
-//     lists do not depend on the launch shape.
+//     groups: entry k of list position q is nbr[(q/32)*K*32 + k*32 + q%32],
+//     so a warp reads one entry for all its lanes in one coalesced access.
+//     An entry packs the neighbour's slot and its cell offset (dcx+1,
+//     dcy+1).  Staged shapes: position = slot.  Global-memory shapes: the
+//     positions of a chunk hold its slots in order of decreasing list
+//     batches and nn[q] names the slot (chunk_lists_sorted).  The
+//     lists' contents do not depend on the launch shape.
 //   * the position window of a chunk is the contiguous (periodically
 //     wrapped) slot range holding every particle of the cells from one row
 //     below the chunk's first cell to one row above its last cell; each step
@@ -642,7 +648,8 @@ __device__ __forceinline__ void chunk_lists_sorted(const SysDev &S, int set, con
 // another order).  Then a counting sort of all particles by cell, particles
 // inside one cell ordered by id, so the order -- and therefore every force
 // sum -- is reproducible and independent of the launch shape; then the
-// neighbour lists.  Six grid barriers.  Padding slots keep perm = -1 (set at
+// neighbour lists.  Six grid barriers (seven in the global-memory shapes,
+// whose lists other CTAs read next).  Padding slots keep perm = -1 (set at
 // creation).
 enum RebuildMode { RB_ALL = 1, RB_NONE = 2 };
 
@@ -985,7 +992,7 @@ __device__ __forceinline__ void kick_drift(const RepDev &R, typename V2<T>::type
 //     accumulated bound on displacements since the last rebuild reaches half
 //     the skin: until then no pair can have come within rc without being
 //     listed.  One bound for the batch, so every replica is rebuilt together
-//     (one sort, six grid barriers); for a single replica this is the rule
+//     (one sort, six or seven grid barriers); for a single replica this is the rule
 //     of the resident engine, which keeps one bound per replica.
 // CTAs per SM the register allocation is sized for: half occupancy (64
 // registers), or with DENSE full occupancy (32 registers: the spills cost
