@@ -55,8 +55,8 @@ __global__ void k_init(SysDev S, const double *x, const double *y, const double 
     S.pid[0][slot] = id;
 }
 
-// Energy partials of one replica summed in a fixed order.
-__global__ void k_sum_energy(const double *epart, int g0, int g1, double *out4) {
+// Energy partials of one replica summed in a fixed order by one CTA.
+__device__ __forceinline__ void sum_energy_cta(const double *epart, int g0, int g1, double *out4) {
     __shared__ double sh[4][256];
     double a[4] = {0, 0, 0, 0};
     for (int g = g0 + threadIdx.x; g < g1; g += 256)
@@ -69,6 +69,16 @@ __global__ void k_sum_energy(const double *epart, int g0, int g1, double *out4) 
         __syncthreads();
     }
     if (threadIdx.x < 4) out4[threadIdx.x] = sh[threadIdx.x][0];
+}
+
+__global__ void k_sum_energy(const double *epart, int g0, int g1, double *out4) {
+    sum_energy_cta(epart, g0, g1, out4);
+}
+
+// every replica at once, one CTA per replica: the same sums as k_sum_energy
+__global__ void k_sum_energy_batch(const double *epart, const RepDev *reps, double *out) {
+    const RepDev &R = reps[blockIdx.x];
+    sum_energy_cta(epart, R.pbase / 32, (R.pbase + R.cap) / 32, out + 4 * (size_t)blockIdx.x);
 }
 
 struct FeqArgs {
@@ -1534,6 +1544,28 @@ int md_energy(md_system *s, int32_t rep, double *out4) {
     k_sum_energy<<<1, 256, 0, s->st>>>(s->d_epart, R.pbase / 32, (R.pbase + R.cap) / 32, s->d_small);
     MD_CUDA_TRY(cudaGetLastError());
     MD_CUDA_TRY(cudaMemcpyAsync(out4, s->d_small, 4 * sizeof(double), cudaMemcpyDeviceToHost, s->st));
+    return sync_status(s);
+}
+
+int md_energy_batch(md_system *s, double *out) {
+    if (!s || !out) return fail(MD_E_ARG, "md_energy_batch: bad arguments");
+    ObsArgs a{};
+    a.epart = s->d_epart;
+    int rc = observe(s, a);
+    if (rc) return rc;
+    const size_t bytes = sizeof(double) * 4 * (size_t)s->nrep;
+    cudaPointerAttributes at{};
+    const bool dev = cudaPointerGetAttributes(&at, out) == cudaSuccess && at.type == cudaMemoryTypeDevice;
+    cudaGetLastError();
+    double *dst = out;
+    if (!dev) MD_CUDA_TRY(cudaMallocAsync((void **)&dst, bytes, s->st));
+    k_sum_energy_batch<<<s->nrep, 256, 0, s->st>>>(s->d_epart, s->d_reps, dst);
+    cudaError_t e = cudaGetLastError();
+    if (!dev) {
+        if (e == cudaSuccess) e = cudaMemcpyAsync(out, dst, bytes, cudaMemcpyDeviceToHost, s->st);
+        cudaFreeAsync(dst, s->st);
+    }
+    if (e != cudaSuccess) return fail(MD_E_CUDA, "md_energy_batch: %s", cudaGetErrorString(e));
     return sync_status(s);
 }
 

@@ -85,6 +85,7 @@ _SIGS = {
     "md_forces": ([P, P, P, P], C.c_int),
     "md_step_forces": ([P, C.c_int64, P, P], C.c_int),
     "md_energy": ([P, C.c_int32, P], C.c_int),
+    "md_energy_batch": ([P, P], C.c_int),
     "md_checkpoint_bytes": ([P, C.POINTER(C.c_int64)], C.c_int),
     "md_checkpoint_save": ([P, P], C.c_int),
     "md_checkpoint_load": ([P, P], C.c_int),
@@ -298,6 +299,13 @@ class System:
     def energy(self, rep=0):
         out = np.zeros(4)
         _check(load().md_energy(self.h, rep, _ptr(out)))
+        return out
+
+    def energy_batch(self):
+        """[n_rep, 4] (kinetic, shifted potential, P_x, P_y) of every replica,
+        from one evaluation of the state; row r equals energy(r) bit for bit."""
+        out = np.zeros((len(self.params), 4))
+        _check(load().md_energy_batch(self.h, _ptr(out)))
         return out
 
     def hist_raw(self, rep=0, lg=0, dxi=0):

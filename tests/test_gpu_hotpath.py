@@ -151,7 +151,8 @@ def test_dynamic_tail_bit_identical_to_dealt_chunks(mdlg):
 @pytest.mark.parametrize("prec", [0, 1])
 def test_energy_matches_oracle(mdlg, orc, prec):
     """md_energy of each replica equals the oracle's kinetic energy, shifted
-    potential energy and momentum on the same state."""
+    potential energy and momentum on the same state; md_energy_batch gives
+    every replica's four values bit for bit."""
     spec = [(3000, 0.25, 2.0), (5000, 0.08, 20.0), (4000, 0.15, 1.0)]
     params, cat = [], [[], [], [], []]
     for r, (n, phi, T) in enumerate(spec):
@@ -165,12 +166,15 @@ def test_energy_matches_oracle(mdlg, orc, prec):
     x, y, vx, vy = s.get_state()
     cell, ox, oy = (t.cpu().numpy() for t in s.get_raw())
     base = 0
+    eb = s.energy_batch()
+    assert eb.shape == (len(spec), 4)
     for r, (n, _, _) in enumerate(spec):
         info = s.rep_info(r)
         nc, h, Le = int(info.ncell), float(info.h), float(info.L_eff)
         sl = slice(base, base + n)
         base += n
         g = s.energy(r)
+        assert np.array_equal(eb[r], g), (r, eb[r], g)
         o = orc.energy(x[sl], y[sl], vx[sl], vy[sl], Le)
         assert abs(g[0] - o[0]) <= 1e-12 * o[0]
         pabs = np.sum(np.abs(vx[sl])), np.sum(np.abs(vy[sl]))

@@ -107,7 +107,8 @@ def test_surrogate_pipeline_beats_md_free_baseline(mdlg):
     at query time) must beat the ballistic Gaussian (the other MD-free
     prediction) and stay within 1.5e-2 of every measured class (measured
     9.1e-3 with this small set and short training; the full pipeline of
-    surrogate.main reaches 1.3e-3)."""
+    surrogate.main reaches 1.4e-3 with one network, 1.05e-3 with its
+    four-network predictor)."""
     from paper_2101_01160_gb300 import surrogate
 
     tr = surrogate.generate(31, n_rep=96, steps=8000, n_equil=2000, n_min=2048, n_max=8192)
