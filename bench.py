@@ -25,6 +25,7 @@ from __future__ import annotations
 
 import argparse
 import json
+import math
 import os
 import subprocess
 import sys
@@ -44,11 +45,25 @@ DT = 5e-4
 EVERY = 400
 MD_PER_STEP = 400
 W = 4
-# Verlet skin of the ensemble's neighbour lists (an implementation choice:
+# Verlet skin of each replica's neighbour lists (an implementation choice:
 # lists hold pairs within rc + skin and are rebuilt when a displacement
-# reaches skin/2; results do not depend on it).  Measured on this ensemble:
-# 0.35-0.45 take about 77 ms per 400 steps, 0.5 about 80, 0.6 82, 0.8 86.
-SKIN = 0.6   # Verlet skin of the ensemble (measured sweep, see the MD kernel's profile)
+# reaches skin/2; the physics does not depend on it).  The global engine
+# rebuilds every replica when any replica's displacement bound, in units of
+# its own half skin, is used up, so a skin proportional to the thermal speed
+# sqrt(T) lets every replica use its bound at about the same rate and gives
+# the slower replicas shorter lists.  Measured on this ensemble (ms per
+# 400-step bench step): one skin for all 0.6: 64.8; 0.7 sqrt(T/20), at least
+# 0.2: 63.2; 0.6 sqrt(T/20), at least 0.15: 63.5; 0.6 (T/20)^0.35, at least
+# 0.2: 63.5.
+SKIN_HOT, SKIN_T, SKIN_MIN = 0.7, 20.0, 0.2
+
+
+def skin_of(T):
+    """Verlet skin of a replica at temperature T."""
+    return max(SKIN_MIN, SKIN_HOT * math.sqrt(T / SKIN_T))
+
+
+SKIN_TEXT = "Verlet skin 0.7 sqrt(T/20) per replica (at least 0.2)"
 BYTES_PER_PARTICLE_STEP = 40.0      # FP32 cell + offset: 20 B state read + 20 B written
 RESIDENT_SLAB_PARTICLES = 8192      # own particles one resident slab (one SM's shared memory) holds
 L2_BYTES = 129 * 2 ** 20
@@ -71,12 +86,12 @@ def _peaks(key="hbm_gbs", fallback=6800.0):
 # of k_md_persistent<float,256,1> (the launch shape the autotuner picks),
 # copied here with its provenance; it is reported only for that kernel and
 # launch shape, and must be re-measured when the kernel changes.
-MD_TRAFFIC = {"kernel": "k_md_persistent<float,256,1>", "bytes_per_launch": 182509082266,
+MD_TRAFFIC = {"kernel": "k_md_persistent<float,256,1>", "bytes_per_launch": 176736049050,
               "source": "ncu --metrics dram__bytes_read.sum,dram__bytes_write.sum,gpu__time_duration.sum "
                         "over every launch of 'bench.py --steps 2 --warmup 3 --no-cpu-baseline "
                         "--no-variants' (one pass), mean of the five 400-step launches of warm-up "
-                        "and timed region (Verlet skin 0.6): 132.7 GB read + 49.8 GB written, 79.9 B "
-                        "per particle-step"}
+                        "and timed region (Verlet skin 0.7 sqrt(T/20) per replica, at least 0.2): "
+                        "127.7 GB read + 49.0 GB written, 77.4 B per particle-step"}
 
 
 def _cpu_model():
@@ -97,19 +112,21 @@ def _cpu_model():
     return "unknown"
 
 
-def _flops_per_particle_step(ens, skin=SKIN, rc=2.5):
+def _flops_per_particle_step(ens, skin=None, rc=2.5):
     """Algorithmic flops of one particle-step of the list-based LJ step
     (full neighbour lists, each pair evaluated from both sides), averaged
     over the particles of the ensemble: per listed pair the pair vector and
     r^2 (5 flops), per pair within rc the force (13 more: 1/r^2, s^6, the
     force factor and two multiply-adds), per particle the two half kicks,
     the drift and the speed bound (16).  Mean counts from the density:
-    pi rc^2 n pairs within rc, pi (rc + skin)^2 n listed."""
+    pi rc^2 n pairs within rc, pi (rc + skin)^2 n listed (skin: one for all,
+    else each replica's skin_of(T))."""
     tot, num = 0.0, 0.0
-    for (n, L, *_rest) in ens:
+    for (n, L, *rest) in ens:
         dens = n / (L * L)
         within = np.pi * rc * rc * dens
-        listed = np.pi * (rc + skin) ** 2 * dens
+        sk = skin if skin is not None else skin_of(rest[1])
+        listed = np.pi * (rc + sk) ** 2 * dens
         num += n * (5.0 * listed + 13.0 * within + 16.0)
         tot += n
     return num / tot
@@ -188,7 +205,7 @@ def ensemble(seed_offset=0, reps=None):
 
 
 WORKLOAD = (f"batched ensemble: {N_REP} replicas, N log-uniform [4096,65536], phi U[0.02,0.30], "
-            f"T U[1,20], FP32 cell+offset, dt 5e-4, Verlet skin {SKIN}, sampling every 400 steps "
+            f"T U[1,20], FP32 cell+offset, dt 5e-4, {SKIN_TEXT}, sampling every 400 steps "
             "(dt_lg 0.2) on dx~1, W=4; 400 MD steps + batched f_eq stage per step")
 
 
@@ -202,7 +219,7 @@ def _ensemble_particles(seed_offset=0):
 
 def _ens_params(mdlg, ens, prec):
     return [mdlg.make_params(n, L, dt=DT, precision=prec, W=W, n_equil=0, lg_every=(EVERY,),
-                             lx=(int(round(L)),), skin=SKIN) for (n, L, _, _, _) in ens]
+                             lx=(int(round(L)),), skin=skin_of(T)) for (n, L, _, T, _) in ens]
 
 
 def _time_variant(mdlg, torch, params, st, md_steps, reps=3):
@@ -586,9 +603,10 @@ def run_ours(args):
     # a replica that fits one SM's shared memory for a whole launch (the
     # resident engine's slab capacity) counted with no HBM traffic
     t_bound = 0.0
-    for (n, L, *_rest) in ens:
+    for e in ens:
+        n = e[0]
         b = 0.0 if n <= RESIDENT_SLAB_PARTICLES else BYTES_PER_PARTICLE_STEP * n * MD_PER_STEP
-        f = _flops_per_particle_step([(n, L)]) * n * MD_PER_STEP
+        f = _flops_per_particle_step([e]) * n * MD_PER_STEP
         t_bound += max(b / (peak * 1e9), f / (peaks["fp32_tflops"] * 1e12))
     composite = {"bound_ms": t_bound * 1e3, "kernel_ms": kern_avg_s * 1e3, "frac": t_bound / kern_avg_s,
                  "resident_below_particles": RESIDENT_SLAB_PARTICLES,
@@ -670,7 +688,7 @@ def _equal_accuracy(mdlg, torch, windows=32, target=1e-4):
     states = [inputs.lattice_gas_state(n, L, T1, seed=5000 + r) for r in range(R)]
     cat = [np.concatenate([getattr(st, f) for st in states]) for f in ("x", "y", "vx", "vy")]
     p = mdlg.make_params(n, L, dt=DT, precision=mdlg.MD_FP32_CELLOFF, W=W, n_equil=neq, lg_every=(EVERY,),
-                         lx=(int(round(L)),), skin=SKIN)
+                         lx=(int(round(L)),), skin=skin_of(T1))
     s = mdlg.System([p] * R, *cat)
     shape = s.autotune(50)
     s.close()
