@@ -224,6 +224,7 @@ using namespace mdlg;
 extern "C" int mdlg_bin(const md_snapshot *t0, const md_snapshot *t1, int64_t n, int32_t lx,
                         int32_t W, int32_t *hist_out, int64_t *overflow_out, double *mom_out,
                         void *stream) {
+    mdlg::Range range_("mdlg_bin");
     int rc = bin_check_args(t0, t1, n, lx, W, hist_out, overflow_out, mom_out);
     if (rc) return rc;
     cudaStream_t st = (cudaStream_t)stream;
@@ -248,6 +249,7 @@ extern "C" int mdlg_bin(const md_snapshot *t0, const md_snapshot *t1, int64_t n,
 extern "C" int mdlg_bin_noalloc(const md_snapshot *t0, const md_snapshot *t1, int64_t n, int32_t lx,
                                 int32_t W, int32_t *hist_out, int64_t *overflow_out, double *mom_out,
                                 void *stream) {
+    mdlg::Range range_("mdlg_bin_noalloc");
     int rc = bin_check_args(t0, t1, n, lx, W, hist_out, overflow_out, mom_out);
     if (rc) return rc;
     const int grid = bin_grid(n);

@@ -9,7 +9,20 @@
 
 #include "mdlg.h"
 
+#include <nvtx3/nvToolsExt.h>
+
 namespace mdlg {
+
+// A named NVTX range over the host side of one library call (argument checks
+// and the enqueue of its launches), so that a profiler can pick out the
+// call's kernels by name (ncu --nvtx --nvtx-include "md_step/").  NVTX is
+// header-only; without an attached tool a range is one predictable branch.
+struct Range {
+    explicit Range(const char *name) { nvtxRangePushA(name); }
+    ~Range() { nvtxRangePop(); }
+    Range(const Range &) = delete;
+    Range &operator=(const Range &) = delete;
+};
 
 // ---------------------------------------------------------------- errors
 void set_error(const std::string &msg);

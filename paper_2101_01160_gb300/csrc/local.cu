@@ -219,6 +219,7 @@ using namespace mdlg;
 
 extern "C" int mdlg_site_occupation(const md_snapshot *t0, const md_snapshot *t1, int64_t n, int32_t lx,
                                     int32_t W, int32_t *n_out, int32_t *overflow_out, void *stream) {
+    mdlg::Range range_("mdlg_site_occupation");
     if (!t0 || !t1 || !n_out || !overflow_out) return fail(MD_E_ARG, "mdlg_site_occupation: NULL argument");
     if (n < 0 || n >= (int64_t)1 << 31) return fail(MD_E_ARG, "mdlg_site_occupation: n out of [0, 2^31)");
     if (n > 0 && (!t0->cell || !t0->off_x || !t0->off_y || !t1->cell || !t1->off_x || !t1->off_y))
@@ -254,6 +255,7 @@ extern "C" int mdlg_site_occupation(const md_snapshot *t0, const md_snapshot *t1
 
 extern "C" int mdlg_collision(const int32_t *n_t, const int32_t *n_next, int32_t lx, int32_t W, double scale,
                               int32_t *xi_out, double *omega_out, void *stream) {
+    mdlg::Range range_("mdlg_collision");
     if (!n_t || !n_next || (!xi_out && !omega_out)) return fail(MD_E_ARG, "mdlg_collision: NULL argument");
     if (lx < 1) return fail(MD_E_ARG, "mdlg_collision: lx must be >= 1");
     if (W < 0 || W > MD_MAX_W) return fail(MD_E_ARG, "mdlg_collision: W out of [0,%d]", MD_MAX_W);

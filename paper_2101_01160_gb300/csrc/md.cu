@@ -1082,6 +1082,7 @@ extern "C" {
 
 int md_init_batch(const md_params *p, int32_t n_rep, const double *x, const double *y,
                   const double *vx, const double *vy, void *stream, md_system **out) {
+    mdlg::Range range_("md_init_batch");
     if (!p || !out || n_rep < 1) return fail(MD_E_ARG, "md_init_batch: bad arguments");
     if (n_rep > MD_MAX_REP) return fail(MD_E_LIMIT, "md_init_batch: more than %d replicas", MD_MAX_REP);
     *out = nullptr;
@@ -1277,6 +1278,7 @@ void md_destroy(md_system *s) {
 }
 
 int md_step(md_system *s, int64_t nsteps) {
+    mdlg::Range range_("md_step");
     if (!s || nsteps < 0) return fail(MD_E_ARG, "md_step: bad arguments");
     if (nsteps == 0) return MD_OK;
     int rc = s->engine == 1 ? launch_resident(s, nsteps) : launch_persistent(s, nsteps, 0);
@@ -1338,6 +1340,7 @@ int md_checkpoint_bytes(md_system *s, int64_t *bytes) {
 }
 
 int md_checkpoint_save(md_system *s, void *buf) {
+    mdlg::Range range_("md_checkpoint_save");
     if (!s || !buf) return fail(MD_E_ARG, "md_checkpoint_save: NULL argument");
     int rc = ensure_sorted(s);
     if (rc) return rc;
@@ -1369,6 +1372,7 @@ int md_checkpoint_save(md_system *s, void *buf) {
 }
 
 int md_checkpoint_load(md_system *s, const void *buf) {
+    mdlg::Range range_("md_checkpoint_load");
     if (!s || !buf) return fail(MD_E_ARG, "md_checkpoint_load: NULL argument");
     CkptHeader h;
     std::memcpy(&h, buf, sizeof(h));
@@ -1516,6 +1520,7 @@ int md_forces(md_system *s, double *fx, double *fy, double *fabs_sum) {
 }
 
 int md_step_forces(md_system *s, int64_t nsteps, double *fx, double *fy) {
+    mdlg::Range range_("md_step_forces");
     if (!s || nsteps < 1 || !fx || !fy) return fail(MD_E_ARG, "md_step_forces: bad arguments");
     const size_t bytes = sizeof(double) * s->ntot;
     double *tmp = nullptr;
@@ -1548,6 +1553,7 @@ int md_energy(md_system *s, int32_t rep, double *out4) {
 }
 
 int md_energy_batch(md_system *s, double *out) {
+    mdlg::Range range_("md_energy_batch");
     if (!s || !out) return fail(MD_E_ARG, "md_energy_batch: bad arguments");
     ObsArgs a{};
     a.epart = s->d_epart;
@@ -1589,6 +1595,7 @@ int md_hist_raw(md_system *s, int32_t rep, int32_t lg, int32_t dxi, int64_t *his
 
 int feq_measured(md_system *s, int32_t rep, int32_t lg, int32_t dxi, int32_t symmetrize,
                  double *P_out, double *stderr_out, md_feq_stats *stats) {
+    mdlg::Range range_("feq_measured");
     if (!s || !P_out || rep < 0 || rep >= s->nrep || lg < 0 || lg >= s->n_lg || dxi < 0 ||
         dxi >= s->n_dx)
         return fail(MD_E_ARG, "feq_measured: bad arguments");
@@ -1652,6 +1659,7 @@ int md_hist_blocks(md_system *s, int32_t rep, int32_t lg, int32_t dxi, int32_t *
 
 int feq_bootstrap(md_system *s, int32_t lg, int32_t dxi, int32_t symmetrize, int32_t n_resamples, uint64_t seed,
                   double *sigma_out) {
+    mdlg::Range range_("feq_bootstrap");
     if (!s || !sigma_out || lg < 0 || lg >= s->n_lg || dxi < 0 || dxi >= s->n_dx || n_resamples < 2 ||
         n_resamples > (1 << 20))
         return fail(MD_E_ARG, "feq_bootstrap: bad arguments");
@@ -1687,6 +1695,7 @@ int feq_bootstrap(md_system *s, int32_t lg, int32_t dxi, int32_t symmetrize, int
 }
 
 int feq_batch(md_system *s, int32_t lg, int32_t dxi, int32_t symmetrize, double *out) {
+    mdlg::Range range_("feq_batch");
     if (!s || !out || lg < 0 || lg >= s->n_lg || dxi < 0 || dxi >= s->n_dx)
         return fail(MD_E_ARG, "feq_batch: bad arguments");
     FeqBatchArgs A{};
@@ -1733,6 +1742,7 @@ std::map<std::tuple<int, int, int, int>, std::vector<double>> g_tune_costs;   //
 }
 
 int md_autotune(md_system *s, int64_t steps_per_trial, int32_t *best3) {
+    mdlg::Range range_("md_autotune");
     if (!s || steps_per_trial < 1) return fail(MD_E_ARG, "md_autotune: bad arguments");
     int lg2 = 0;
     while ((1ll << lg2) < s->ntot) ++lg2;

@@ -1092,6 +1092,7 @@ int mlp_get_params(mlp_model *m, float *params) {
 }
 
 int mlp_forward(mlp_model *m, const float *X, int64_t M, float *P_out, void *stream) {
+    mdlg::Range range_("mlp_forward");
     if (!m || !X || !P_out || M < 1) return fail(MD_E_ARG, "mlp_forward: bad arguments");
     if ((uintptr_t)X & 15) return fail(MD_E_ARG, "mlp_forward: X must be 16-byte aligned");
     cudaStream_t st = (cudaStream_t)stream;
@@ -1153,6 +1154,7 @@ int mlp_grad(mlp_model *m, const float *X, const float *T, int32_t B, float *gra
 
 int mlp_train_step(mlp_model *m, const float *X, const float *T, int32_t B, float lr,
                    float *loss_out, void *stream) {
+    mdlg::Range range_("mlp_train_step");
     int rc = mlp_grad(m, X, T, B, nullptr, loss_out, stream);
     if (rc) return rc;
     cudaStream_t st = (cudaStream_t)stream;

@@ -190,6 +190,7 @@ using namespace mdlg;
 
 extern "C" int mdlg_disp_hist(const md_snapshot *t0, const md_snapshot *t1, int64_t n, double width,
                               int32_t nbins, int64_t *hist_out, int64_t *outside_out, void *stream) {
+    mdlg::Range range_("mdlg_disp_hist");
     if (!t0 || !t1 || !hist_out || !outside_out) return fail(MD_E_ARG, "mdlg_disp_hist: NULL argument");
     if (n < 0 || n >= (int64_t)1 << 31) return fail(MD_E_ARG, "mdlg_disp_hist: n out of [0, 2^31)");
     if (n > 0 && (!t0->cell || !t0->off_x || !t0->off_y || !t1->cell || !t1->off_x || !t1->off_y))
