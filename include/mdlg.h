@@ -297,12 +297,13 @@ int md_step_forces(md_system *s, int64_t nsteps, double *fx, double *fy);
  * potential, P_x, P_y} (host, FP64).  Synchronises. */
 int md_energy(md_system *s, int32_t rep, double *out4);
 
-/* Energies of every replica from one evaluation of the current state:
- * out[4 r + k] = component k of md_energy(s, r, .) for replica r, bit for
- * bit (the same partial sums in the same order).  out: host or device,
- * FP64, [n_rep][4].  The kinetic temperature of replica r in two
- * dimensions with zero total momentum is out[4 r] / (N_r - 1).
- * Synchronises. */
+/* Energies (Sec. 4: kinetic, shifted Lennard-Jones potential, momentum) of
+ * every replica from one evaluation of the current state: out[4 r + k] =
+ * component k of md_energy(s, r, .) for replica r, bit for bit (the same
+ * partial sums in the same order).  out: host or device, FP64, [n_rep][4],
+ * caller-owned.  The kinetic temperature of replica r in two dimensions with
+ * zero total momentum is out[4 r] / (N_r - 1).  MD_E_ARG for a null handle
+ * or out.  Synchronises. */
 int md_energy_batch(md_system *s, double *out);
 
 /* Raw integer histogram totals of (rep, lg, dxi): hist (host, int64,
