@@ -1,7 +1,8 @@
 """Pins of the oracle's Lennard-Jones force and velocity-Verlet dynamics (Sec. 4):
 exact potential values, force = -grad of the potential by finite differences,
 Newton's third law, cell list = all pairs, NVE energy error scaling as dt^2,
-momentum conservation, time reversibility, and the ballistic ideal gas whose
+momentum conservation, time reversibility, the energy of a hand-made
+configuration, and the ballistic ideal gas whose
 measured equilibrium must equal the Gaussian one (Sec. 1) within sampling
 error."""
 
@@ -151,3 +152,26 @@ def test_moments_independent_of_lattice_count(orc):
     dy -= L * np.round(dy / L)
     assert abs(a["mom"][0, 0] - np.sum(dx ** 2 + dy ** 2)) < 1e-9 * a["mom"][0, 0]
     assert abs(a["mom"][0, 1] - np.sum(dx ** 4 + dy ** 4)) < 1e-9 * a["mom"][0, 1]
+
+
+@pytest.mark.parametrize("eps,sigma,mass", [(1.0, 1.0, 1.0), (1.5, 1.1, 2.0)])
+def test_energy_of_a_hand_made_configuration(orc, eps, sigma, mass):
+    """Energy, momentum and the shifted potential summed once per pair under
+    the minimum image (Sec. 4), written out for four particles in a 10 x 10
+    box: pairs (0,1) at r = 1.1, (0,2) at 1.5 across the x wrap and (0,3)
+    at 2.4 are inside rc = 2.5; every other pair is beyond it."""
+    L, rc = 10.0, 2.5
+    x = np.array([1.0, 2.1, 9.5, 1.0])
+    y = np.array([1.0, 1.0, 1.0, 3.4])
+    vx = np.array([0.5, -1.0, 2.0, 0.0])
+    vy = np.array([1.5, 0.25, -0.75, -2.0])
+
+    def v_shift(r):
+        return 4 * eps * ((sigma / r) ** 12 - (sigma / r) ** 6) - 4 * eps * ((sigma / rc) ** 12 - (sigma / rc) ** 6)
+
+    ke = 0.5 * mass * float(np.sum(vx * vx + vy * vy))
+    pe = v_shift(1.1) + v_shift(1.5) + v_shift(2.4)
+    out = orc.energy(x, y, vx, vy, L, rc=rc, eps=eps, sigma=sigma, mass=mass)
+    assert abs(out[0] - ke) <= 1e-14 * ke
+    assert abs(out[1] - pe) <= 1e-12 * abs(pe)
+    assert abs(out[2] - mass * vx.sum()) <= 1e-15 and abs(out[3] - mass * vy.sum()) <= 1e-15
