@@ -243,7 +243,8 @@ int md_rep_info(md_system *s, int32_t rep, md_rep_info_t *out);
  * as if not called).  Synchronises. */
 int md_get_state(md_system *s, double *x, double *y, double *vx, double *vy);
 
-/* Replaces positions and velocities (same layout as md_init); keeps the
+/* Replaces positions and velocities (same layout as md_init; host or device
+ * FP64 arrays, read in stream order on the system's stream); keeps the
  * histograms and the step counter.  Synchronises. */
 int md_set_state(md_system *s, const double *x, const double *y, const double *vx,
                  const double *vy);

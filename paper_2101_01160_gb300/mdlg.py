@@ -249,7 +249,20 @@ class System:
         return out
 
     def set_state(self, x, y, vx, vy):
-        arrs = [np.ascontiguousarray(a, dtype=np.float64) for a in (x, y, vx, vy)]
+        """Host arrays (converted to FP64), or contiguous FP64 CUDA tensors
+        of n_total elements each, read on the system's stream (the caller
+        orders any copy into them before the call)."""
+        arrs = (x, y, vx, vy)
+        if all(getattr(a, "is_cuda", False) for a in arrs):
+            import torch
+
+            for a in arrs:
+                if a.dtype != torch.float64 or not a.is_contiguous() or a.numel() != self.n_total:
+                    raise ValueError(f"set_state: device arrays must be contiguous float64 of {self.n_total}")
+        else:
+            arrs = [np.ascontiguousarray(a, dtype=np.float64) for a in arrs]
+            if any(a.size != self.n_total for a in arrs):
+                raise ValueError(f"set_state: arrays must hold {self.n_total} values")
         _check(load().md_set_state(self.h, *[_ptr(a) for a in arrs]))
 
     def _raw_buffers(self):
