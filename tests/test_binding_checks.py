@@ -50,3 +50,21 @@ def test_field_checks():
         mdlg.collision(n, n.to(torch.int64), 1)
     with pytest.raises(ValueError, match="CUDA"):
         mdlg.collision(n, n, 1)
+
+
+def test_set_state_checks():
+    """md_set_state reads n_total FP64 values per array from host or device
+    memory, so the binding refuses shorter host arrays and non-FP64,
+    non-contiguous or mis-sized device tensors before the call."""
+    import types
+
+    fake = types.SimpleNamespace(n_total=8, h=None)
+    ok = [np.zeros(8) for _ in range(4)]
+    with pytest.raises(ValueError, match="hold 8 values"):
+        mdlg.System.set_state(fake, np.zeros(7), *ok[1:])
+    if torch.cuda.is_available():
+        dev = [torch.zeros(8, dtype=torch.float64, device="cuda") for _ in range(4)]
+        with pytest.raises(ValueError, match="float64 of 8"):
+            mdlg.System.set_state(fake, dev[0].float(), *dev[1:])
+        with pytest.raises(ValueError, match="float64 of 8"):
+            mdlg.System.set_state(fake, torch.zeros(16, dtype=torch.float64, device="cuda")[::2], *dev[1:])
